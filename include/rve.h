@@ -1,0 +1,196 @@
+/*
+ * rve.h - C ABI of the GB300 FFT-Galerkin strain-gradient crystal-plasticity
+ * increment (Haouala, Lucarini, LLorca, Segurado, arXiv:1910.01946).
+ *
+ * One handle holds one voxelised FCC polycrystal (a representative volume
+ * element, RVE) and advances it one strain increment per rve_step:
+ *   - Nye tensor G = -curl Fp by the rotated-scheme spectral derivative
+ *     (App. A Eq. kas, App. B Eq. nyeindexfourier);
+ *   - GND densities by the minimum-norm inverse of Eq. defA2 (Eq. mingnd);
+ *   - Taylor hardening (Eq. Taylor_hard) and mean free path (Eq. meanfree);
+ *   - per-voxel implicit crystal-plasticity update and consistent tangent
+ *     (Sec. 2.1, Eqs. 1-5, power law, Eq. Piola);
+ *   - Newton-Raphson with conjugate gradients on the Galerkin equilibrium
+ *     G*(K : dF) = -G*(P - Pbar) under mixed macroscopic control
+ *     (Sec. 2.2, Eqs. weakarbi, eql_discrete2, linequil2ast);
+ *   - commit of Fp, S and the SSD densities (Kocks-Mecking, Eq. kocks).
+ *
+ * Conventions for every entry point below:
+ *   - voxel index v = x + n0*(y + n1*z) (x fastest); voxels are cubes of
+ *     edge h = L/n0 (rve_options.L);
+ *   - 3x3 tensors are row-major, component index 3*i + j;
+ *   - fields are structure-of-arrays: component c of voxel v at [c*nvox + v];
+ *   - units: MPa for moduli and stresses, metres for lengths, m^-2 for
+ *     dislocation densities, seconds for time;
+ *   - all device memory is the caller's: rve_create carves its state out of
+ *     one caller-owned device workspace of rve_workspace_bytes() bytes, which
+ *     must outlive the handle; the library itself calls no cudaMalloc for
+ *     field storage (it allocates only a small pinned host scalar block);
+ *   - every call is issued on the CUDA stream given at rve_create and
+ *     returns an rve_status; no exception or abort crosses the ABI.  On a
+ *     non-OK status rve_last_error() gives a message.  A device error
+ *     (RVE_ECUDA) leaves the handle unusable.
+ */
+#ifndef RVE_H
+#define RVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RVE_OK = 0,
+  RVE_EINVAL = 1,         /* bad argument: sizes, pointers, out-of-range values */
+  RVE_ENOMEM = 2,         /* workspace too small */
+  RVE_ECUDA = 3,          /* a CUDA call failed */
+  RVE_ENOCONV_LOCAL = 4,  /* a voxel's implicit update did not converge */
+  RVE_ENOCONV_CG = 5,     /* conjugate gradients hit max_cg */
+  RVE_ENOCONV_NEWTON = 6, /* Newton-Raphson hit max_newton or could not decrease the residual */
+  RVE_ENAN = 7            /* a non-finite residual */
+} rve_status;
+
+typedef struct rve_s rve_t;
+
+/* Material (Sec. 2.1, Tables 1-2).  Critical resolved shear stress
+ *   tauc^a = tau0 + alpha mu b sqrt(sum_b q^ab (rho_SSD^b + rho_GND^b)),
+ * the paper's Eq. Taylor_hard being tau0 = 0, alpha = 1, unnormalised q. */
+typedef struct {
+  double C11, C12, C44;  /* cubic elastic constants [MPa] */
+  double b;              /* Burgers vector length [m] */
+  double mu;             /* shear modulus in the Taylor law [MPa]; <= 0: 3 C44 (C11-C12)/(4 C44 + C11 - C12) */
+  double tau0;           /* lattice friction [MPa] */
+  double alpha;          /* Taylor coefficient [-] */
+  double q[6];           /* interaction coefficients: self, coplanar, collinear, Hirth, glissile, Lomer (Table 1) */
+  int32_t q_normalise;   /* nonzero: divide q by its self coefficient */
+  double gdot0;          /* reference slip rate [1/s] */
+  double n;              /* power-law exponent (Table 1 rate sensitivity m = 0.05 -> n = 1/m = 20) */
+  double K;              /* similitude coefficient in the mean free path (Eq. meanfree) [-] */
+  double yc;             /* annihilation distance (Eq. kocks) [m] */
+  double rho0_total;     /* initial SSD density summed over the 12 systems [m^-2] */
+  int32_t gnd_enabled;   /* 0: GND densities switched off ("infinite grain size", Sec. 3) */
+} rve_material;
+
+typedef struct {
+  double L;              /* RVE edge along x [m]; voxel edge h = L / n0 */
+  double newton_tol;     /* stop when rms(G*(P - Pbar)) <= newton_tol * max(|<P>|, 1e-4 mu) */
+  double cg_tol;         /* CG relative residual */
+  double local_tol;      /* local update: max |r| <= local_tol * mu */
+  int32_t max_newton, max_cg, max_local, max_halvings;
+  int32_t extrapolate;   /* nonzero: predict the increment from the previous one */
+  int32_t precision;     /* 0: FP64 throughout (the only value accepted) */
+} rve_options;
+
+#define RVE_MAX_NEWTON_LOG 64
+typedef struct {
+  int32_t converged;
+  int32_t newton_iters;
+  int32_t cg_iters_total;
+  int32_t local_max_iters;
+  int32_t local_failures;
+  int32_t halvings;
+  double residual;                              /* final relative residual */
+  double seconds;                               /* host wall time of the call */
+  int32_t cg_iters[RVE_MAX_NEWTON_LOG];         /* per Newton iteration */
+  double residuals[RVE_MAX_NEWTON_LOG + 1];     /* relative residual per Newton iteration */
+} rve_step_info;
+
+/* Field selectors for rve_get_fields / rve_set_fields (double unless noted).
+ * Committed state (the end of the last converged increment):
+ *   F, P, FP, SIGMA (Cauchy P F^T / det F): 9 components; S: 6 (Voigt 11, 22,
+ *   33, 23, 13, 12; second Piola-Kirchhoff stress in the intermediate
+ *   configuration, sample axes); RHO_SSD: 12 (slip systems); VM: 1 (von Mises
+ *   stress of the Cauchy stress); GRAIN: 1 (int32).
+ * Hardening of the last increment (computed from Fp at its start, or by
+ * rve_eval_hardening from the committed Fp):
+ *   NYE: 9; RHO_GND18: 18 (12 edge segments in slip-system order, then 6
+ *   screw segments along [0 1 -1], [1 0 -1], [1 -1 0], [0 1 1], [1 0 1],
+ *   [1 1 0]); RHO_GND, TAUC: 12.
+ * Last local evaluation (the converged one after rve_step, or the one made by
+ * rve_eval_constitutive):
+ *   P_EVAL: 9; S_EVAL: 6; DGAM: 12 (slip increments); TANGENT: 81
+ *   (K_ijkl = dP_ij / dF_kl at component 27*i + 9*j + 3*k + l). */
+enum {
+  RVE_FIELD_F = 0, RVE_FIELD_P = 1, RVE_FIELD_FP = 2, RVE_FIELD_S = 3,
+  RVE_FIELD_SIGMA = 4, RVE_FIELD_RHO_SSD = 5, RVE_FIELD_RHO_GND = 6,
+  RVE_FIELD_RHO_GND18 = 7, RVE_FIELD_NYE = 8, RVE_FIELD_VM = 9,
+  RVE_FIELD_TAUC = 10, RVE_FIELD_DGAM = 11, RVE_FIELD_TANGENT = 12,
+  RVE_FIELD_GRAIN = 13, RVE_FIELD_P_EVAL = 14, RVE_FIELD_S_EVAL = 15
+};
+
+/* Bytes of device workspace needed for an n0 x n1 x n2 grid of n_grains
+ * grains.  n0 and n1 must be even, every size a product of 2s and 3s with
+ * 2 <= n0, n1 <= 512 and 1 <= n2 <= 512.  Returns 0 for unsupported sizes,
+ * grain counts or precision. */
+size_t rve_workspace_bytes(int n0, int n1, int n2, int n_grains, int precision);
+
+/* Create a handle.
+ *   grain_id: host, n0*n1*n2 int32 in [0, n_grains), voxel order as above;
+ *   quat: host, 4*n_grains doubles (w, x, y, z), rotation crystal -> sample
+ *         (normalised here);
+ *   mat, opt: host structs, copied;
+ *   d_workspace: device pointer, 256-byte aligned, ws_bytes >= rve_workspace_bytes();
+ *   cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Initial state: F = Fp = I, S = 0, rho_SSD = rho0_total / 12 on every system.
+ * Errors: RVE_EINVAL (sizes, ids, pointers, options), RVE_ENOMEM (workspace),
+ * RVE_ECUDA. */
+rve_status rve_create(const int32_t* grain_id, int n0, int n1, int n2,
+                      const double* quat, int n_grains,
+                      const rve_material* mat, const rve_options* opt,
+                      void* d_workspace, size_t ws_bytes, void* cuda_stream,
+                      rve_t** out);
+
+/* One strain increment of length dt (Sec. 2.2).  dFbar: host, 9 increments
+ * of the macroscopic deformation gradient, used where strain_mask[c] != 0
+ * (strain-controlled); Pbar: host, 9 prescribed macroscopic first
+ * Piola-Kirchhoff stresses, used where strain_mask[c] == 0.  info: host,
+ * may be NULL.  On any status but RVE_OK the state is the last committed
+ * increment (the call is atomic). */
+rve_status rve_step(rve_t* rve, const double dFbar[9], const uint8_t strain_mask[9],
+                    const double Pbar[9], double dt, rve_step_info* info);
+
+/* Volume averages of the first Piola-Kirchhoff stress and of the Cauchy
+ * stress P F^T / det F over the committed state; host outputs. */
+rve_status rve_get_macro_stress(rve_t* rve, double P[9], double sigma[9]);
+
+/* Copy one field (see the selectors) to dst (host or device memory per
+ * dst_is_device); bytes >= ncomp * nvox * element size, else RVE_EINVAL. */
+rve_status rve_get_fields(rve_t* rve, uint32_t which, void* dst, size_t bytes, int dst_is_device);
+
+/* Overwrite one committed state field (F, FP or RHO_SSD) from src (host or
+ * device per src_is_device, bytes == ncomp * nvox * 8).  Used to set up a
+ * test state; other selectors give RVE_EINVAL. */
+rve_status rve_set_fields(rve_t* rve, uint32_t which, const void* src, size_t bytes, int src_is_device);
+
+/* Kernel-level entry points on the committed state (used for per-step parity
+ * checks):
+ *   rve_eval_hardening: Nye tensor, GND densities and tauc from the committed
+ *     Fp and SSD densities (fields NYE, RHO_GND18, RHO_GND, TAUC);
+ *   rve_eval_constitutive: rve_eval_hardening, then the local update and
+ *     tangent at the committed F over an increment dt from the committed Fp
+ *     (warm start: the committed S); fields P_EVAL, S_EVAL, DGAM, TANGENT.
+ *     local_max_iters / local_failures (host, nullable) receive the largest
+ *     local iteration count and the number of voxels that did not converge;
+ *   rve_project: Y = G*(X) for device fields X, Y (9 * nvox doubles each,
+ *     may alias) under the given strain mask (zero mode: components with
+ *     strain_mask[c] == 0 kept, the others zeroed). */
+rve_status rve_eval_hardening(rve_t* rve);
+rve_status rve_eval_constitutive(rve_t* rve, double dt, int32_t* local_max_iters, int32_t* local_failures);
+rve_status rve_project(rve_t* rve, const uint8_t strain_mask[9], const double* d_X, double* d_Y);
+
+/* Checkpoint: host buffer of rve_checkpoint_bytes() bytes holding F, Fp, S,
+ * rho_SSD, the previous increment and the macro history; rve_restore checks
+ * sizes and a magic/version word (RVE_EINVAL on mismatch). */
+size_t rve_checkpoint_bytes(const rve_t* rve);
+rve_status rve_checkpoint(rve_t* rve, void* host_buf, size_t bytes);
+rve_status rve_restore(rve_t* rve, const void* host_buf, size_t bytes);
+
+const char* rve_last_error(const rve_t* rve);
+void rve_destroy(rve_t* rve);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RVE_H */

@@ -1,0 +1,78 @@
+// Device helpers shared by the kernels of the GB300 path: complex arithmetic,
+// the FCC slip-system table in the crystal frame and small 3x3 algebra.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define RVE_HD __host__ __device__ __forceinline__
+
+struct cplx { double x, y; };
+RVE_HD cplx cmk(double a, double b) { cplx c; c.x = a; c.y = b; return c; }
+RVE_HD cplx cadd(cplx a, cplx b) { return cmk(a.x + b.x, a.y + b.y); }
+RVE_HD cplx csub(cplx a, cplx b) { return cmk(a.x - b.x, a.y - b.y); }
+RVE_HD cplx cmul(cplx a, cplx b) { return cmk(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x)); }
+RVE_HD cplx cconj(cplx a) { return cmk(a.x, -a.y); }
+RVE_HD cplx cscale(cplx a, double s) { return cmk(a.x * s, a.y * s); }
+// multiply by (sign * i): sign = -1 forward, +1 inverse
+RVE_HD cplx cmul_i(cplx a, int sign) { return sign > 0 ? cmk(-a.y, a.x) : cmk(a.y, -a.x); }
+
+// FCC {111}<110> slip systems, crystal frame, unnormalised integer vectors.
+// Plane normals m' in {(111), (-111), (1-11), (11-1)} (|m'| = sqrt 3), three
+// <110> directions s' (|s'| = sqrt 2) per plane; the unit Schmid tensor is
+// s (x) m = s' m'^T / sqrt 6.  The order is the one the whole library (and its
+// field outputs) uses for slip-system indices 0..11.
+__device__ __constant__ const int8_t FCC_S[12][3] = {
+    {0, 1, -1}, {-1, 0, 1}, {1, -1, 0},
+    {0, 1, -1}, {1, 0, 1}, {1, 1, 0},
+    {0, 1, 1}, {1, 0, -1}, {1, 1, 0},
+    {0, 1, 1}, {1, 0, 1}, {1, -1, 0}};
+__device__ __constant__ const int8_t FCC_M[12][3] = {
+    {1, 1, 1}, {1, 1, 1}, {1, 1, 1},
+    {-1, 1, 1}, {-1, 1, 1}, {-1, 1, 1},
+    {1, -1, 1}, {1, -1, 1}, {1, -1, 1},
+    {1, 1, -1}, {1, 1, -1}, {1, 1, -1}};
+
+// Voigt order of a symmetric tensor: 11, 22, 33, 23, 13, 12
+#define V_I(a) ((a) < 3 ? (a) : ((a) == 3 ? 1 : 0))
+#define V_J(a) ((a) < 3 ? (a) : ((a) == 5 ? 1 : 2))
+
+RVE_HD void mat3_mul(const double* A, const double* B, double* C) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      C[3 * i + j] = fma(A[3 * i], B[j], fma(A[3 * i + 1], B[3 + j], A[3 * i + 2] * B[6 + j]));
+}
+// C = A^T B
+RVE_HD void mat3_tmul(const double* A, const double* B, double* C) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      C[3 * i + j] = fma(A[i], B[j], fma(A[3 + i], B[3 + j], A[6 + i] * B[6 + j]));
+}
+// C = A B^T
+RVE_HD void mat3_mult(const double* A, const double* B, double* C) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      C[3 * i + j] = fma(A[3 * i], B[3 * j], fma(A[3 * i + 1], B[3 * j + 1], A[3 * i + 2] * B[3 * j + 2]));
+}
+RVE_HD double mat3_inv(const double* A, double* B) {
+  double c00 = A[4] * A[8] - A[5] * A[7];
+  double c01 = A[5] * A[6] - A[3] * A[8];
+  double c02 = A[3] * A[7] - A[4] * A[6];
+  double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+  double id = 1.0 / det;
+  B[0] = c00 * id;
+  B[1] = (A[2] * A[7] - A[1] * A[8]) * id;
+  B[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+  B[3] = c01 * id;
+  B[4] = (A[0] * A[8] - A[2] * A[6]) * id;
+  B[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+  B[6] = c02 * id;
+  B[7] = (A[1] * A[6] - A[0] * A[7]) * id;
+  B[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+  return det;
+}

@@ -1,0 +1,444 @@
+// Per-voxel kernels of the strain-gradient crystal-plasticity model (FP64,
+// one voxel per thread, structure-of-arrays fields):
+//
+//   k_hardening    GND densities from the Nye tensor by the minimum-norm
+//                  inverse of G = A rho (Eqs. defA2, mingnd), the Taylor
+//                  critical resolved shear stress (Eq. Taylor_hard, with the
+//                  lattice friction tau0 and Taylor coefficient alpha) and the
+//                  mean free path (Eq. meanfree), frozen for the increment.
+//   k_constitutive the implicit update of Sec. 2.1 (Eqs. 1-5, power law,
+//                  Eq. Piola) by Newton on the second Piola-Kirchhoff stress S,
+//                  and the consistent tangent dP/dF (Eq. linequil2ast).
+//
+// Everything inside a voxel is done in its grain's crystal frame, where the
+// stiffness is cubic (three constants) and the Schmid tensors s (x) m are
+// compile-time constants with entries 0, +-1/sqrt6: with X~ = R^T X R for
+// every second-order tensor (R: crystal -> sample), the update is covariant,
+// so F is rotated in and P, dP/dF are rotated out.
+//
+// Time integration (the paper gives none): backward Euler,
+//   Fp = (I + sum_a dgam^a s^a (x) m^a) Fp_prev,
+//   dgam^a = dt gdot0 |tau^a / tauc^a|^n sgn tau^a,  tau^a = S : s^a (x) m^a,
+// residual r(S) = S - C : (Fe^T Fe - I)/2, Fe = F Fp^-1, solved from a warm
+// start with the exact Jacobian and step halving (a step is taken only if it
+// lowers max|r| and keeps every |dgam| <= dgam_max).
+#include "common.cuh"
+#include "rve_internal.h"
+
+namespace {
+
+constexpr double INV_SQRT6 = 0.40824829046386301637;
+
+__device__ __forceinline__ double ipow(double x, int n) {
+  double r = 1.0;
+  while (n) {
+    if (n & 1) r *= x;
+    x *= x;
+    n >>= 1;
+  }
+  return r;
+}
+
+// tau^a = S : s^a (x) m^a for symmetric S in Voigt order (11,22,33,23,13,12)
+__device__ __forceinline__ double resolved(const double* S, int a) {
+  const double s0 = FCC_S[a][0], s1 = FCC_S[a][1], s2 = FCC_S[a][2];
+  const double m0 = FCC_M[a][0], m1 = FCC_M[a][1], m2 = FCC_M[a][2];
+  double t = s0 * m0 * S[0] + s1 * m1 * S[1] + s2 * m2 * S[2] + (s1 * m2 + s2 * m1) * S[3] +
+             (s0 * m2 + s2 * m0) * S[4] + (s0 * m1 + s1 * m0) * S[5];
+  return t * INV_SQRT6;
+}
+
+// d tau^a / d S_voigt
+__device__ __forceinline__ void tau_grad(int a, double* w) {
+  const double s0 = FCC_S[a][0], s1 = FCC_S[a][1], s2 = FCC_S[a][2];
+  const double m0 = FCC_M[a][0], m1 = FCC_M[a][1], m2 = FCC_M[a][2];
+  w[0] = s0 * m0 * INV_SQRT6; w[1] = s1 * m1 * INV_SQRT6; w[2] = s2 * m2 * INV_SQRT6;
+  w[3] = (s1 * m2 + s2 * m1) * INV_SQRT6; w[4] = (s0 * m2 + s2 * m0) * INV_SQRT6; w[5] = (s0 * m1 + s1 * m0) * INV_SQRT6;
+}
+
+// M += g * s^a (x) m^a
+__device__ __forceinline__ void add_schmid(double* M, int a, double g) {
+  const double gs = g * INV_SQRT6;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) M[3 * i + j] = fma(gs, (double)(FCC_S[a][i] * FCC_M[a][j]), M[3 * i + j]);
+}
+
+// cubic stiffness applied to a symmetric strain given by its tensor components
+// (E11, E22, E33, E23, E13, E12) -> stress in Voigt order
+__device__ __forceinline__ void cubic(const Consts& c, const double* E, double* S) {
+  S[0] = fma(c.C11, E[0], c.C12 * (E[1] + E[2]));
+  S[1] = fma(c.C11, E[1], c.C12 * (E[0] + E[2]));
+  S[2] = fma(c.C11, E[2], c.C12 * (E[0] + E[1]));
+  S[3] = 2.0 * c.C44 * E[3];
+  S[4] = 2.0 * c.C44 * E[4];
+  S[5] = 2.0 * c.C44 * E[5];
+}
+
+__device__ __forceinline__ void sym_full(const double* v, double* X) {
+  X[0] = v[0]; X[4] = v[1]; X[8] = v[2];
+  X[5] = X[7] = v[3];
+  X[2] = X[6] = v[4];
+  X[1] = X[3] = v[5];
+}
+
+struct Eval {
+  double tau[12], dg[12];
+  double Minv[9];
+  double Ce[6];   // symmetric, Voigt order
+  double r[6];
+  double rn;      // max |r|, +inf when rejected
+};
+
+// Evaluate the residual at S; A = FeTr^T FeTr (full 3x3, symmetric).
+__device__ void evaluate(const Consts& c, const double* S, const double* A, const double* tauc, double dt, Eval& e) {
+  double M[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  bool bad = false;
+#pragma unroll
+  for (int a = 0; a < 12; ++a) {
+    const double t = resolved(S, a);
+    const double x = t / tauc[a];
+    const double ax = fabs(x);
+    const double xn = c.n_int ? ipow(ax, c.n_int) : pow(ax, c.n);
+    double g = dt * c.gdot0 * xn;
+    bad |= !(g <= c.dgam_max);
+    g = copysign(g, x);
+    e.tau[a] = t;
+    e.dg[a] = g;
+  }
+  if (bad) {
+    e.rn = INFINITY;
+    return;
+  }
+#pragma unroll
+  for (int a = 0; a < 12; ++a) add_schmid(M, a, e.dg[a]);
+  mat3_inv(M, e.Minv);
+  double B[9], Ce[9];
+  mat3_mul(A, e.Minv, B);
+  mat3_tmul(e.Minv, B, Ce);
+  e.Ce[0] = Ce[0]; e.Ce[1] = Ce[4]; e.Ce[2] = Ce[8];
+  e.Ce[3] = 0.5 * (Ce[5] + Ce[7]); e.Ce[4] = 0.5 * (Ce[2] + Ce[6]); e.Ce[5] = 0.5 * (Ce[1] + Ce[3]);
+  double E[6] = {0.5 * (e.Ce[0] - 1.0), 0.5 * (e.Ce[1] - 1.0), 0.5 * (e.Ce[2] - 1.0),
+                 0.5 * e.Ce[3], 0.5 * e.Ce[4], 0.5 * e.Ce[5]};
+  double Sn[6];
+  cubic(c, E, Sn);
+  double rn = 0.0;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    e.r[k] = S[k] - Sn[k];
+    rn = fmax(rn, fabs(e.r[k]));
+  }
+  e.rn = isfinite(rn) ? rn : INFINITY;
+}
+
+// J = I - sum_a c^a (x) w^a with c^a = -dgp^a C : sym(Ce S0^a Minv)
+__device__ void jacobian(const Consts& c, const Eval& e, const double* tauc, double dt, double* J, double* dgp) {
+#pragma unroll
+  for (int i = 0; i < 36; ++i) J[i] = (i % 7 == 0) ? 1.0 : 0.0;
+  double Cf[9];
+  sym_full(e.Ce, Cf);
+#pragma unroll
+  for (int a = 0; a < 12; ++a) {
+    const double x = fabs(e.tau[a] / tauc[a]);
+    const double xn1 = c.n_int ? ipow(x, c.n_int - 1) : pow(x, c.n - 1.0);
+    const double gp = dt * c.gdot0 * c.n * xn1 / tauc[a];
+    dgp[a] = gp;
+    // u = Ce s', w = Minv^T m'  (times 1/sqrt6 folded in below)
+    double u[3], w[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      u[i] = Cf[3 * i] * FCC_S[a][0] + Cf[3 * i + 1] * FCC_S[a][1] + Cf[3 * i + 2] * FCC_S[a][2];
+      w[i] = e.Minv[i] * FCC_M[a][0] + e.Minv[3 + i] * FCC_M[a][1] + e.Minv[6 + i] * FCC_M[a][2];
+    }
+    const double f = -gp * INV_SQRT6;
+    double T[6] = {f * u[0] * w[0], f * u[1] * w[1], f * u[2] * w[2], 0.5 * f * (u[1] * w[2] + u[2] * w[1]),
+                   0.5 * f * (u[0] * w[2] + u[2] * w[0]), 0.5 * f * (u[0] * w[1] + u[1] * w[0])};
+    double cv[6];
+    cubic(c, T, cv);
+    double wt[6];
+    tau_grad(a, wt);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) J[6 * i + j] = fma(-cv[i], wt[j], J[6 * i + j]);
+  }
+}
+
+// LU with partial pivoting of a 6x6 matrix in place; piv[k] = row swapped into k
+__device__ void lu6(double* J, int* piv) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    int p = k;
+    double best = fabs(J[6 * k + k]);
+#pragma unroll
+    for (int i = k + 1; i < 6; ++i) {
+      const double v = fabs(J[6 * i + k]);
+      if (v > best) { best = v; p = i; }
+    }
+    piv[k] = p;
+    if (p != k) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        const double t = J[6 * k + j]; J[6 * k + j] = J[6 * p + j]; J[6 * p + j] = t;
+      }
+    }
+    const double inv = 1.0 / J[6 * k + k];
+#pragma unroll
+    for (int i = k + 1; i < 6; ++i) {
+      const double l = J[6 * i + k] * inv;
+      J[6 * i + k] = l;
+#pragma unroll
+      for (int j = k + 1; j < 6; ++j) J[6 * i + j] = fma(-l, J[6 * k + j], J[6 * i + j]);
+    }
+  }
+}
+
+__device__ void lu6_solve(const double* LU, const int* piv, double* b) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const int p = piv[k];
+    if (p != k) { const double t = b[k]; b[k] = b[p]; b[p] = t; }
+  }
+#pragma unroll
+  for (int i = 1; i < 6; ++i)
+#pragma unroll
+    for (int j = 0; j < i; ++j) b[i] = fma(-LU[6 * i + j], b[j], b[i]);
+#pragma unroll
+  for (int i = 5; i >= 0; --i) {
+#pragma unroll
+    for (int j = i + 1; j < 6; ++j) b[i] = fma(-LU[6 * i + j], b[j], b[i]);
+    b[i] /= LU[6 * i + i];
+  }
+}
+
+__global__ void __launch_bounds__(128) k_hardening(
+    size_t nvox, const int32_t* __restrict__ grain, const double* __restrict__ grainR,
+    const double* __restrict__ qhat, const double* __restrict__ Apinv, const int32_t* __restrict__ screw_of,
+    const double* __restrict__ nye, const double* __restrict__ rho_ssd, const double* __restrict__ Fp,
+    double* __restrict__ rho18, double* __restrict__ rho_gnd, double* __restrict__ tauc, double* __restrict__ ell,
+    double* __restrict__ Fp0inv, Consts c) {
+  __shared__ double sq[144], sA[162];
+  __shared__ int sscrew[12];
+  for (int i = threadIdx.x; i < 144; i += blockDim.x) sq[i] = qhat[i];
+  for (int i = threadIdx.x; i < 162; i += blockDim.x) sA[i] = Apinv[i];
+  if (threadIdx.x < 12) sscrew[threadIdx.x] = screw_of[threadIdx.x];
+  __syncthreads();
+  const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nvox) return;
+  double R[9], G[9], T[9], Gt[9];
+  const int g = grain[v];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) R[k] = __ldg(grainR + 9 * g + k);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) G[k] = nye[k * nvox + v];
+  mat3_mul(G, R, T);
+  mat3_tmul(R, T, Gt);       // R^T G R
+  double r18[18];
+#pragma unroll
+  for (int a = 0; a < 18; ++a) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s = fma(sA[9 * a + k], Gt[k], s);
+    r18[a] = s;
+    rho18[a * nvox + v] = s;
+  }
+  double rho[12], sum = 0.0;
+#pragma unroll
+  for (int a = 0; a < 12; ++a) {
+    const double gd = c.gnd_enabled ? fabs(r18[a]) + 0.5 * fabs(r18[12 + sscrew[a]]) : 0.0;
+    rho_gnd[a * nvox + v] = gd;
+    rho[a] = rho_ssd[a * nvox + v] + gd;
+    sum += rho[a];
+  }
+  const double amb = c.alpha * c.mu * c.b;
+#pragma unroll
+  for (int a = 0; a < 12; ++a) {
+    double s = 0.0;
+#pragma unroll
+    for (int b = 0; b < 12; ++b) s = fma(sq[12 * a + b], rho[b], s);
+    tauc[a * nvox + v] = fma(amb, sqrt(s), c.tau0);
+    ell[a * nvox + v] = c.K / sqrt(sum - rho[a]);
+  }
+  double Fpv[9], Fi[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Fpv[k] = Fp[k * nvox + v];
+  mat3_inv(Fpv, Fi);
+  mat3_mul(Fi, R, T);
+  mat3_tmul(R, T, Gt);       // R^T Fp^-1 R
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Fp0inv[k * nvox + v] = Gt[k];
+}
+
+__global__ void __launch_bounds__(128) k_constitutive(
+    size_t nvox, const int32_t* __restrict__ grain, const double* __restrict__ grainR,
+    const double* __restrict__ Fin, const double* __restrict__ xdir, double lambda,
+    const double* __restrict__ Fp0inv, const double* __restrict__ tauc_g, const double* __restrict__ Swarm,
+    double* __restrict__ Pout, double* __restrict__ Kout, double* __restrict__ Sout, double* __restrict__ dgout,
+    int32_t* __restrict__ counters, double dt, Consts c) {
+  const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int iters = 0, failed = 0;
+  if (v < nvox) {
+    double R[9], Fs[9], T[9], Ft[9], Fpi0[9];
+    const int g = grain[v];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) R[k] = __ldg(grainR + 9 * g + k);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      double f = Fin[k * nvox + v];
+      if (lambda != 0.0) f = fma(lambda, xdir[k * nvox + v], f);
+      Fs[k] = f;
+      Fpi0[k] = Fp0inv[k * nvox + v];
+    }
+    mat3_mul(Fs, R, T);
+    mat3_tmul(R, T, Ft);                  // F~ = R^T F R
+    double FeTr[9], A[9];
+    mat3_mul(Ft, Fpi0, FeTr);
+    mat3_tmul(FeTr, FeTr, A);
+    double tauc[12];
+#pragma unroll
+    for (int a = 0; a < 12; ++a) tauc[a] = tauc_g[a * nvox + v];
+    double S[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) S[k] = Swarm[k * nvox + v];
+
+    Eval e;
+    evaluate(c, S, A, tauc, dt, e);
+    if (!(e.rn < INFINITY)) {             // warm start rejected: restart from the elastic-free state
+#pragma unroll
+      for (int k = 0; k < 6; ++k) S[k] = 0.0;
+      evaluate(c, S, A, tauc, dt, e);
+    }
+    double J[36], dgp[12];
+    int piv[6];
+    bool conv = e.rn <= c.local_tol_abs;
+    while (!conv && iters < c.max_local) {
+      jacobian(c, e, tauc, dt, J, dgp);
+      lu6(J, piv);
+      double d[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) d[k] = -e.r[k];
+      lu6_solve(J, piv, d);
+      double lam = 1.0;
+      bool acc = false;
+      for (int hv = 0; hv <= c.max_halvings; ++hv) {
+        double St[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) St[k] = fma(lam, d[k], S[k]);
+        Eval et;
+        evaluate(c, St, A, tauc, dt, et);
+        if (et.rn < e.rn) {
+#pragma unroll
+          for (int k = 0; k < 6; ++k) S[k] = St[k];
+          e = et;
+          acc = true;
+          break;
+        }
+        lam *= 0.5;
+      }
+      ++iters;
+      if (!acc) {                          // no decrease: round-off floor or failure
+        conv = e.rn <= c.floor_abs;
+        break;
+      }
+      conv = e.rn <= c.local_tol_abs;
+    }
+    failed = conv ? 0 : 1;
+
+    // ---- outputs: S, dgam, P and the consistent tangent
+#pragma unroll
+    for (int k = 0; k < 6; ++k) Sout[k * nvox + v] = S[k];
+#pragma unroll
+    for (int a = 0; a < 12; ++a) dgout[a * nvox + v] = e.dg[a];
+    jacobian(c, e, tauc, dt, J, dgp);
+    lu6(J, piv);
+    double Fpinv[9], Fe[9], Sf[9], W[9], Q[9];
+    mat3_mul(Fpi0, e.Minv, Fpinv);
+    mat3_mul(Ft, Fpinv, Fe);
+    sym_full(S, Sf);
+    mat3_mult(Sf, Fpinv, W);             // W = S Fpinv^T
+    mat3_mul(Fpinv, W, Q);               // Q = Fpinv S Fpinv^T
+    {
+      double Pt[9], U[9], P[9];
+      mat3_mul(Ft, Q, Pt);
+      mat3_mult(Pt, R, U);               // P~ R^T
+      mat3_mul(R, U, P);                 // R P~ R^T
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Pout[k * nvox + v] = P[k];
+    }
+#pragma unroll 1
+    for (int kl = 0; kl < 9; ++kl) {
+      const int kk = kl / 3, ll = kl % 3;
+      double a3[3], b3[3];
+#pragma unroll
+      for (int p = 0; p < 3; ++p) { a3[p] = R[3 * kk + p]; b3[p] = R[3 * ll + p]; }
+      // dF~ = a b^T; dEe = sym(Fe^T a (Fpinv^T b)^T)
+      double u[3], w[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        u[i] = Fe[i] * a3[0] + Fe[3 + i] * a3[1] + Fe[6 + i] * a3[2];
+        w[i] = Fpinv[i] * b3[0] + Fpinv[3 + i] * b3[1] + Fpinv[6 + i] * b3[2];
+      }
+      double dE[6] = {u[0] * w[0], u[1] * w[1], u[2] * w[2], 0.5 * (u[1] * w[2] + u[2] * w[1]),
+                      0.5 * (u[0] * w[2] + u[2] * w[0]), 0.5 * (u[0] * w[1] + u[1] * w[0])};
+      double dS[6];
+      cubic(c, dE, dS);
+      lu6_solve(J, piv, dS);
+      double dM[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+      for (int a = 0; a < 12; ++a) add_schmid(dM, a, dgp[a] * resolved(dS, a));
+      double t1[9], dFpi[9], dQ[9], dSf[9], t2[9];
+      mat3_mul(dM, e.Minv, t1);
+      mat3_mul(Fpinv, t1, dFpi);        // (negated below)
+      mat3_mul(dFpi, W, t1);            // dFpinv W with dFpinv = -dFpi
+      sym_full(dS, dSf);
+      mat3_mult(dSf, Fpinv, t2);
+      mat3_mul(Fpinv, t2, dQ);          // Fpinv dS Fpinv^T
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) dQ[3 * i + j] -= t1[3 * i + j] + t1[3 * j + i];
+      double qb[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) qb[j] = Q[3 * j] * b3[0] + Q[3 * j + 1] * b3[1] + Q[3 * j + 2] * b3[2];
+      double dPt[9];
+      mat3_mul(Ft, dQ, dPt);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) dPt[3 * i + j] = fma(a3[i], qb[j], dPt[3 * i + j]);
+      double U[9], dP[9];
+      mat3_mult(dPt, R, U);
+      mat3_mul(R, U, dP);
+#pragma unroll
+      for (int ij = 0; ij < 9; ++ij) Kout[(size_t)(9 * ij + kl) * nvox + v] = dP[ij];
+    }
+  }
+  // counters: warp-aggregated
+  const unsigned full = 0xffffffffu;
+  int mx = __reduce_max_sync(full, iters);
+  int nf = __reduce_add_sync(full, failed);
+  if ((threadIdx.x & 31) == 0) {
+    if (mx) atomicMax(&counters[0], mx);
+    if (nf) atomicAdd(&counters[1], nf);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_hardening(const rve_s* h, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((h->nvox + 127) / 128);
+  k_hardening<<<blocks, 128, 0, s>>>(h->nvox, h->grain, h->grainR, h->qhat, h->Apinv, h->screw_of, h->nye,
+                                     h->rho_ssd, h->Fp, h->rho18, h->rho_gnd, h->tauc, h->ell, h->Fp0inv, h->cst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_constitutive(const rve_s* h, double dt, double lambda, int out_buf, int warm_buf,
+                                cudaStream_t s) {
+  const unsigned blocks = (unsigned)((h->nvox + 127) / 128);
+  const double* warm = warm_buf < 0 ? h->S_c : h->S[warm_buf];
+  k_constitutive<<<blocks, 128, 0, s>>>(h->nvox, h->grain, h->grainR, h->F, h->x, lambda, h->Fp0inv, h->tauc,
+                                        warm, h->P[out_buf], h->K[out_buf], h->S[out_buf], h->dgam[out_buf],
+                                        h->dcount, dt, h->cst);
+  return cudaGetLastError();
+}

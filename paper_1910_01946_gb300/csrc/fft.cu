@@ -1,0 +1,351 @@
+// Hand-written batched 3-D real FFT of the nine tensor-component fields
+// (FP64), with the frequency-space operators of the method fused between the
+// forward and inverse transforms along z:
+//   - the Galerkin projection with mixed control (Sec. 2.2, Eqs. weakarbi,
+//     eql_discrete2) built from the rotated-scheme frequencies (App. A, Eq. kas);
+//   - the Nye tensor G_ij = -eps_jkl d_k Fp_il (App. B, Eq. nyeindexfourier)
+//     with the same rotated-scheme derivative.
+//
+// Layout.  Real fields: [c][z][y][x] (x fastest).  Half spectrum:
+// [c][z][y][kx], kx = 0..n0/2.  Passes (each a kernel, each transform staged
+// in shared memory and done by a mixed-radix 4/2/3 Stockham autosort):
+//   X  (R2C): two real rows y, y+1 packed as one complex row, one length-n0
+//             FFT, then the two half spectra are separated;
+//   Y  (C2C): tiles of consecutive kx columns, length-n1 FFTs;
+//   Z  (C2C + operator + C2C): the three fields of one tensor row i for a tile
+//             of (kx, ky) pencils (both operators act row by row), forward
+//             z FFT, operator, inverse z FFT;
+//   Y^-1, X^-1 (C2R).  The 1/nvox scaling is folded into the operator.
+#include "common.cuh"
+#include "rve_internal.h"
+
+namespace {
+
+struct PlanDev {
+  int n, npass;
+  int radix[RVE_MAX_RADIX_PASSES];
+};
+
+PlanDev to_dev(const FFTPlan& p) {
+  PlanDev d;
+  d.n = p.n;
+  d.npass = p.npass;
+  for (int i = 0; i < RVE_MAX_RADIX_PASSES; ++i) d.radix[i] = p.radix[i];
+  return d;
+}
+
+__device__ __forceinline__ cplx ld_tw(const double2* tw, int idx, int sign) {
+  double2 w = __ldg(tw + idx);
+  return cmk(w.x, sign < 0 ? w.y : -w.y);
+}
+
+// One Stockham pass of radix R over `howmany` contiguous transforms of length
+// N from src to dst (both shared memory).
+__device__ void stockham_pass(const cplx* __restrict__ src, cplx* __restrict__ dst, int N, int howmany,
+                              int R, int Ns, const double2* tw, int sign) {
+  const int nb = N / R;
+  const int total = nb * howmany;
+  const int twstep = N / (Ns * R);
+  for (int b = threadIdx.x; b < total; b += blockDim.x) {
+    const int tr = b / nb;
+    const int j = b - tr * nb;
+    const int k = j % Ns;
+    const cplx* X = src + tr * N;
+    cplx* Y = dst + tr * N;
+    const int d = (j / Ns) * Ns * R + k;
+    if (R == 4) {
+      cplx a0 = X[j], a1 = X[j + nb], a2 = X[j + 2 * nb], a3 = X[j + 3 * nb];
+      if (k) {
+        a1 = cmul(a1, ld_tw(tw, k * twstep, sign));
+        a2 = cmul(a2, ld_tw(tw, 2 * k * twstep, sign));
+        a3 = cmul(a3, ld_tw(tw, 3 * k * twstep, sign));
+      }
+      cplx t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = cmul_i(csub(a1, a3), sign);
+      Y[d] = cadd(t0, t2);
+      Y[d + Ns] = cadd(t1, t3);
+      Y[d + 2 * Ns] = csub(t0, t2);
+      Y[d + 3 * Ns] = csub(t1, t3);
+    } else if (R == 2) {
+      cplx a0 = X[j], a1 = X[j + nb];
+      if (k) a1 = cmul(a1, ld_tw(tw, k * twstep, sign));
+      Y[d] = cadd(a0, a1);
+      Y[d + Ns] = csub(a0, a1);
+    } else {  // R == 3
+      cplx a0 = X[j], a1 = X[j + nb], a2 = X[j + 2 * nb];
+      if (k) {
+        a1 = cmul(a1, ld_tw(tw, k * twstep, sign));
+        a2 = cmul(a2, ld_tw(tw, 2 * k * twstep, sign));
+      }
+      const double s3 = 0.86602540378443864676;  // sqrt(3)/2
+      cplx t = cadd(a1, a2);
+      cplx u = cscale(cmul_i(csub(a1, a2), sign), s3);
+      cplx m = cmk(fma(-0.5, t.x, a0.x), fma(-0.5, t.y, a0.y));
+      Y[d] = cadd(a0, t);
+      Y[d + Ns] = cadd(m, u);
+      Y[d + 2 * Ns] = csub(m, u);
+    }
+  }
+}
+
+// Full transform of `howmany` contiguous length-N sequences; the caller has
+// synchronised after filling `a`.  Returns the buffer that holds the result.
+__device__ cplx* block_fft(cplx* a, cplx* b, const PlanDev& pl, int howmany, const double2* tw, int sign) {
+  int Ns = 1;
+  for (int p = 0; p < pl.npass; ++p) {
+    const int R = pl.radix[p];
+    stockham_pass(a, b, pl.n, howmany, R, Ns, tw, sign);
+    __syncthreads();
+    cplx* t = a; a = b; b = t;
+    Ns *= R;
+  }
+  return a;
+}
+
+// ---------------------------------------------------------------- pass X (R2C)
+__global__ void __launch_bounds__(256) k_fft_x_r2c(const double* __restrict__ in, double2* __restrict__ spec,
+                                                   int n0, int n1, int n2, int nkx, int rpb, PlanDev pl,
+                                                   const double2* __restrict__ tw) {
+  extern __shared__ cplx sm[];
+  cplx* a = sm;
+  cplx* b = sm + rpb * n0;
+  const int f = blockIdx.z, z = blockIdx.y, j0 = blockIdx.x * rpb;
+  const size_t nvox = (size_t)n0 * n1 * n2;
+  const double* src = in + f * nvox + (size_t)z * n1 * n0;
+  for (int e = threadIdx.x; e < rpb * n0; e += blockDim.x) {
+    const int jj = e / n0, x = e - jj * n0;
+    const int y0 = 2 * (j0 + jj);
+    a[e] = cmk(src[(size_t)y0 * n0 + x], src[(size_t)(y0 + 1) * n0 + x]);
+  }
+  __syncthreads();
+  cplx* res = block_fft(a, b, pl, rpb, tw, -1);
+  double2* dst = spec + ((size_t)f * n2 + z) * n1 * nkx;
+  for (int e = threadIdx.x; e < rpb * nkx; e += blockDim.x) {
+    const int jj = e / nkx, k = e - jj * nkx;
+    const cplx zk = res[jj * n0 + k];
+    const cplx zm = cconj(res[jj * n0 + (k == 0 ? 0 : n0 - k)]);
+    const cplx s = cadd(zk, zm), d = csub(zk, zm);
+    const int y0 = 2 * (j0 + jj);
+    dst[(size_t)y0 * nkx + k] = make_double2(0.5 * s.x, 0.5 * s.y);
+    dst[(size_t)(y0 + 1) * nkx + k] = make_double2(0.5 * d.y, -0.5 * d.x);
+  }
+}
+
+// ---------------------------------------------------------------- pass X^-1 (C2R)
+__global__ void __launch_bounds__(256) k_fft_x_c2r(const double2* __restrict__ spec, double* __restrict__ out,
+                                                   int n0, int n1, int n2, int nkx, int rpb, PlanDev pl,
+                                                   const double2* __restrict__ tw) {
+  extern __shared__ cplx sm[];
+  cplx* a = sm;
+  cplx* b = sm + rpb * n0;
+  const int f = blockIdx.z, z = blockIdx.y, j0 = blockIdx.x * rpb;
+  const size_t nvox = (size_t)n0 * n1 * n2;
+  const double2* src = spec + ((size_t)f * n2 + z) * n1 * nkx;
+  for (int e = threadIdx.x; e < rpb * n0; e += blockDim.x) {
+    const int jj = e / n0, k = e - jj * n0;
+    const int y0 = 2 * (j0 + jj);
+    cplx A, B;
+    if (k < nkx) {
+      double2 u = src[(size_t)y0 * nkx + k], v = src[(size_t)(y0 + 1) * nkx + k];
+      A = cmk(u.x, u.y); B = cmk(v.x, v.y);
+    } else {
+      double2 u = src[(size_t)y0 * nkx + (n0 - k)], v = src[(size_t)(y0 + 1) * nkx + (n0 - k)];
+      A = cmk(u.x, -u.y); B = cmk(v.x, -v.y);
+    }
+    a[e] = cmk(A.x - B.y, A.y + B.x);  // A + i B
+  }
+  __syncthreads();
+  cplx* res = block_fft(a, b, pl, rpb, tw, +1);
+  double* dst = out + f * nvox + (size_t)z * n1 * n0;
+  for (int e = threadIdx.x; e < rpb * n0; e += blockDim.x) {
+    const int jj = e / n0, x = e - jj * n0;
+    const int y0 = 2 * (j0 + jj);
+    dst[(size_t)y0 * n0 + x] = res[e].x;
+    dst[(size_t)(y0 + 1) * n0 + x] = res[e].y;
+  }
+}
+
+// ---------------------------------------------------------------- pass Y (C2C)
+__global__ void __launch_bounds__(256) k_fft_y(double2* __restrict__ spec, int n1, int n2, int nkx, int tx,
+                                               PlanDev pl, const double2* __restrict__ tw, int sign) {
+  extern __shared__ cplx sm[];
+  cplx* a = sm;
+  cplx* b = sm + tx * n1;
+  const int f = blockIdx.z, z = blockIdx.y, kx0 = blockIdx.x * tx;
+  double2* base = spec + ((size_t)f * n2 + z) * n1 * nkx;
+  for (int e = threadIdx.x; e < tx * n1; e += blockDim.x) {
+    const int y = e / tx, t = e - y * tx;
+    const int kx = kx0 + t;
+    double2 v = kx < nkx ? base[(size_t)y * nkx + kx] : make_double2(0.0, 0.0);
+    a[t * n1 + y] = cmk(v.x, v.y);
+  }
+  __syncthreads();
+  cplx* res = block_fft(a, b, pl, tx, tw, sign);
+  for (int e = threadIdx.x; e < tx * n1; e += blockDim.x) {
+    const int y = e / tx, t = e - y * tx;
+    const int kx = kx0 + t;
+    if (kx < nkx) {
+      cplx v = res[t * n1 + y];
+      base[(size_t)y * nkx + kx] = make_double2(v.x, v.y);
+    }
+  }
+}
+
+struct OpTables {
+  const double* tan0; const double* tan1; const double* tan2;
+  const int8_t* nyq0; const int8_t* nyq1; const int8_t* nyq2;
+  const double2* ph0; const double2* ph1; const double2* ph2;
+};
+
+// ---------------------------------------------------------------- pass Z + operator
+__global__ void __launch_bounds__(256) k_fft_z_op(double2* __restrict__ spec, int n1, int n2, int nkx, int tx,
+                                                  PlanDev pl, const double2* __restrict__ tw, OpTables T,
+                                                  SpecParams sp) {
+  extern __shared__ cplx sm[];
+  const int cnt = 3 * tx * n2;
+  cplx* a = sm;
+  cplx* b = sm + cnt;
+  const int i = blockIdx.z, ky = blockIdx.y, kx0 = blockIdx.x * tx;
+  const size_t zstride = (size_t)n1 * nkx;
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const int c = e / (tx * n2);
+    const int rem = e - c * tx * n2;
+    const int z = rem / tx, t = rem - z * tx;
+    const int kx = kx0 + t;
+    const size_t f = 3 * i + c;
+    double2 v = kx < nkx ? spec[(f * n2 + z) * zstride + (size_t)ky * nkx + kx] : make_double2(0.0, 0.0);
+    a[(c * tx + t) * n2 + z] = cmk(v.x, v.y);
+  }
+  __syncthreads();
+  cplx* res = block_fft(a, b, pl, 3 * tx, tw, -1);
+  cplx* oth = (res == a) ? b : a;
+  for (int e = threadIdx.x; e < tx * n2; e += blockDim.x) {
+    const int t = e / n2, z = e - t * n2;
+    const int kx = kx0 + t;
+    cplx X0 = res[(0 * tx + t) * n2 + z], X1 = res[(1 * tx + t) * n2 + z], X2 = res[(2 * tx + t) * n2 + z];
+    cplx Y0, Y1, Y2;
+    if (kx >= nkx) {
+      Y0 = Y1 = Y2 = cmk(0.0, 0.0);
+    } else if (sp.op == OP_PROJECT) {
+      if (kx == 0 && ky == 0 && z == 0) {
+        if (sp.mean_out) {
+          sp.mean_out[3 * i + 0] = X0.x * sp.inv_nvox;
+          sp.mean_out[3 * i + 1] = X1.x * sp.inv_nvox;
+          sp.mean_out[3 * i + 2] = X2.x * sp.inv_nvox;
+        }
+        const double nv = 1.0 / sp.inv_nvox;
+        Y0 = sp.keep[3 * i + 0] ? cmk((X0.x - nv * sp.shift[3 * i + 0]) * sp.inv_nvox, X0.y * sp.inv_nvox) : cmk(0.0, 0.0);
+        Y1 = sp.keep[3 * i + 1] ? cmk((X1.x - nv * sp.shift[3 * i + 1]) * sp.inv_nvox, X1.y * sp.inv_nvox) : cmk(0.0, 0.0);
+        Y2 = sp.keep[3 * i + 2] ? cmk((X2.x - nv * sp.shift[3 * i + 2]) * sp.inv_nvox, X2.y * sp.inv_nvox) : cmk(0.0, 0.0);
+      } else {
+        const int q0 = T.nyq0[kx], q1 = T.nyq1[ky], q2 = T.nyq2[z];
+        double u0, u1, u2;
+        if (q0 + q1 + q2 >= 2) {
+          u0 = u1 = u2 = 0.0;
+        } else if (q0 + q1 + q2 == 1) {
+          u0 = q0; u1 = q1; u2 = q2;
+        } else {
+          const double t0 = T.tan0[kx], t1 = T.tan1[ky], t2 = T.tan2[z];
+          const double inv = rsqrt(fma(t0, t0, fma(t1, t1, t2 * t2)));
+          u0 = t0 * inv; u1 = t1 * inv; u2 = t2 * inv;
+        }
+        // (G X)_ij = u_j sum_l X_il u_l  (scaled by 1/nvox)
+        cplx s = cmk(fma(X0.x, u0, fma(X1.x, u1, X2.x * u2)), fma(X0.y, u0, fma(X1.y, u1, X2.y * u2)));
+        s = cscale(s, sp.inv_nvox);
+        Y0 = cscale(s, u0); Y1 = cscale(s, u1); Y2 = cscale(s, u2);
+      }
+    } else {  // OP_CURL: G_ij = -eps_jkl D_k Fp_il
+      const double2 e0 = T.ph0[kx], e1 = T.ph1[ky], e2 = T.ph2[z];
+      const cplx p0 = cmk(1.0 + e0.x, e0.y), p1 = cmk(1.0 + e1.x, e1.y), p2 = cmk(1.0 + e2.x, e2.y);
+      const cplx m0 = cmk(e0.x - 1.0, e0.y), m1 = cmk(e1.x - 1.0, e1.y), m2 = cmk(e2.x - 1.0, e2.y);
+      const double sc = sp.inv4h * sp.inv_nvox;
+      const cplx D0 = cscale(cmul(m0, cmul(p1, p2)), sc);
+      const cplx D1 = cscale(cmul(p0, cmul(m1, p2)), sc);
+      const cplx D2 = cscale(cmul(p0, cmul(p1, m2)), sc);
+      Y0 = csub(cmul(D2, X1), cmul(D1, X2));
+      Y1 = csub(cmul(D0, X2), cmul(D2, X0));
+      Y2 = csub(cmul(D1, X0), cmul(D0, X1));
+    }
+    oth[(0 * tx + t) * n2 + z] = Y0;
+    oth[(1 * tx + t) * n2 + z] = Y1;
+    oth[(2 * tx + t) * n2 + z] = Y2;
+  }
+  __syncthreads();
+  cplx* res2 = block_fft(oth, res, pl, 3 * tx, tw, +1);
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const int c = e / (tx * n2);
+    const int rem = e - c * tx * n2;
+    const int z = rem / tx, t = rem - z * tx;
+    const int kx = kx0 + t;
+    if (kx < nkx) {
+      const size_t f = 3 * i + c;
+      cplx v = res2[(c * tx + t) * n2 + z];
+      spec[(f * n2 + z) * zstride + (size_t)ky * nkx + kx] = make_double2(v.x, v.y);
+    }
+  }
+}
+
+int rows_per_block(int n0, int n1) {
+  int r = 1024 / n0;
+  if (r < 1) r = 1;
+  while (r > 1 && (n1 / 2) % r) --r;
+  if (r > n1 / 2) r = n1 / 2;
+  return r;
+}
+int tile_y(int n1) {
+  int t = 1024 / n1;
+  if (t > 16) t = 16;
+  return t < 1 ? 1 : t;
+}
+int tile_z(int n2) {
+  int t = 512 / n2;
+  if (t > 16) t = 16;
+  return t < 1 ? 1 : t;
+}
+
+}  // namespace
+
+void make_plan(int n, FFTPlan* p) {
+  p->n = n;
+  p->npass = 0;
+  int m = n;
+  while (m % 4 == 0) { p->radix[p->npass++] = 4; m /= 4; }
+  if (m % 2 == 0) { p->radix[p->npass++] = 2; m /= 2; }
+  while (m % 3 == 0) { p->radix[p->npass++] = 3; m /= 3; }
+  if (m != 1) p->npass = -1;  // unsupported length
+}
+
+cudaError_t launch_fft_forward(const rve_s* h, const double* in, cudaStream_t s) {
+  const int rpb = rows_per_block(h->n0, h->n1);
+  dim3 gx(h->n1 / 2 / rpb, h->n2, 9);
+  size_t shx = 2 * (size_t)rpb * h->n0 * sizeof(cplx);
+  k_fft_x_r2c<<<gx, 256, shx, s>>>(in, h->spec, h->n0, h->n1, h->n2, h->nkx, rpb, to_dev(h->plan[0]), h->ax[0].tw);
+  const int ty = tile_y(h->n1);
+  dim3 gy((h->nkx + ty - 1) / ty, h->n2, 9);
+  size_t shy = 2 * (size_t)ty * h->n1 * sizeof(cplx);
+  k_fft_y<<<gy, 256, shy, s>>>(h->spec, h->n1, h->n2, h->nkx, ty, to_dev(h->plan[1]), h->ax[1].tw, -1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fft_op(const rve_s* h, const SpecParams& sp, cudaStream_t s) {
+  const int tz = tile_z(h->n2);
+  dim3 g((h->nkx + tz - 1) / tz, h->n1, 3);
+  size_t sh = 2 * 3 * (size_t)tz * h->n2 * sizeof(cplx);
+  OpTables T;
+  T.tan0 = h->ax[0].tanh_; T.tan1 = h->ax[1].tanh_; T.tan2 = h->ax[2].tanh_;
+  T.nyq0 = h->ax[0].nyq; T.nyq1 = h->ax[1].nyq; T.nyq2 = h->ax[2].nyq;
+  T.ph0 = h->ax[0].ph; T.ph1 = h->ax[1].ph; T.ph2 = h->ax[2].ph;
+  k_fft_z_op<<<g, 256, sh, s>>>(h->spec, h->n1, h->n2, h->nkx, tz, to_dev(h->plan[2]), h->ax[2].tw, T, sp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fft_inverse(const rve_s* h, double* out, cudaStream_t s) {
+  const int ty = tile_y(h->n1);
+  dim3 gy((h->nkx + ty - 1) / ty, h->n2, 9);
+  size_t shy = 2 * (size_t)ty * h->n1 * sizeof(cplx);
+  k_fft_y<<<gy, 256, shy, s>>>(h->spec, h->n1, h->n2, h->nkx, ty, to_dev(h->plan[1]), h->ax[1].tw, +1);
+  const int rpb = rows_per_block(h->n0, h->n1);
+  dim3 gx(h->n1 / 2 / rpb, h->n2, 9);
+  size_t shx = 2 * (size_t)rpb * h->n0 * sizeof(cplx);
+  k_fft_x_c2r<<<gx, 256, shx, s>>>(h->spec, out, h->n0, h->n1, h->n2, h->nkx, rpb, to_dev(h->plan[0]), h->ax[0].tw);
+  return cudaGetLastError();
+}

@@ -1,0 +1,719 @@
+// C ABI and host orchestration of one strain increment (Sec. 2.2 of the
+// paper): Nye tensor and hardening, predictor, Newton-Raphson with conjugate
+// gradients on G*(K : dF) = -G*(P - Pbar) (Eq. linequil2ast), backtracking
+// on the residual norm, commit.  Every kernel runs on the caller's stream;
+// the host reads back only a few scalars per iteration.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "rve_internal.h"
+
+namespace {
+
+const uint32_t CKPT_MAGIC = 0x43455652u;  // "RVEC"
+const uint32_t CKPT_VERSION = 1;
+
+#define RVE_CUDA(h, call)                                                          \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      (h)->err = std::string(#call) + ": " + cudaGetErrorString(e_);              \
+      return RVE_ECUDA;                                                            \
+    }                                                                              \
+  } while (0)
+
+#define RVE_TRY(call)                   \
+  do {                                  \
+    rve_status s_ = (call);             \
+    if (s_ != RVE_OK) return s_;        \
+  } while (0)
+
+bool good_len(int n, int lo) {
+  if (n < lo || n > 512) return false;
+  FFTPlan p;
+  make_plan(n, &p);
+  return p.npass >= 0;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Workspace layout: carve() walks the same sequence for sizing and for
+// assigning pointers.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    size_t o = off;
+    off = align256(off + count * sizeof(T));
+    return base ? reinterpret_cast<T*>(base + o) : nullptr;
+  }
+};
+
+void carve(rve_s* h, Carver& c) {
+  const size_t nv = h->nvox;
+  h->grain = c.take<int32_t>(nv);
+  h->grainR = c.take<double>(9 * (size_t)h->ngrains);
+  h->qhat = c.take<double>(144);
+  h->Apinv = c.take<double>(162);
+  h->screw_of = c.take<int32_t>(12);
+  const int ns[3] = {h->n0, h->n1, h->n2};
+  for (int a = 0; a < 3; ++a) {
+    h->ax[a].tw = c.take<double2>(ns[a]);
+    h->ax[a].tanh_ = c.take<double>(ns[a]);
+    h->ax[a].nyq = c.take<int8_t>(ns[a]);
+    h->ax[a].ph = c.take<double2>(ns[a]);
+  }
+  h->F_c = c.take<double>(9 * nv);
+  h->Fp = c.take<double>(9 * nv);
+  h->S_c = c.take<double>(6 * nv);
+  h->rho_ssd = c.take<double>(12 * nv);
+  h->dF_last = c.take<double>(9 * nv);
+  h->P_c = c.take<double>(9 * nv);
+  h->nye = c.take<double>(9 * nv);
+  h->rho18 = c.take<double>(18 * nv);
+  h->rho_gnd = c.take<double>(12 * nv);
+  h->tauc = c.take<double>(12 * nv);
+  h->ell = c.take<double>(12 * nv);
+  h->Fp0inv = c.take<double>(9 * nv);
+  h->F = c.take<double>(9 * nv);
+  for (int b = 0; b < 2; ++b) {
+    h->P[b] = c.take<double>(9 * nv);
+    h->K[b] = c.take<double>(81 * nv);
+    h->S[b] = c.take<double>(6 * nv);
+    h->dgam[b] = c.take<double>(12 * nv);
+  }
+  h->R = c.take<double>(9 * nv);
+  h->x = c.take<double>(9 * nv);
+  h->r = c.take<double>(9 * nv);
+  h->p = c.take<double>(9 * nv);
+  h->t = c.take<double>(9 * nv);
+  h->q = c.take<double>(9 * nv);
+  h->spec = c.take<double2>(9 * h->nspec);
+  h->partial = c.take<double>(27 * (size_t)RVE_RED_BLOCKS);
+  h->dscal = c.take<double>(64);
+  h->dcount = c.take<int32_t>(16);
+}
+
+// ---- host tables (crystallography written from the geometry of FCC slip) ----
+const int SL_S[12][3] = {{0, 1, -1}, {-1, 0, 1}, {1, -1, 0}, {0, 1, -1}, {1, 0, 1}, {1, 1, 0},
+                         {0, 1, 1}, {1, 0, -1}, {1, 1, 0}, {0, 1, 1}, {1, 0, 1}, {1, -1, 0}};
+const int SL_M[12][3] = {{1, 1, 1}, {1, 1, 1}, {1, 1, 1}, {-1, 1, 1}, {-1, 1, 1}, {-1, 1, 1},
+                         {1, -1, 1}, {1, -1, 1}, {1, -1, 1}, {1, 1, -1}, {1, 1, -1}, {1, 1, -1}};
+const int SCREW[6][3] = {{0, 1, -1}, {1, 0, -1}, {1, -1, 0}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
+
+int idot(const int* a, const int* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// interaction class of systems (a, b): 0 self, 1 coplanar, 2 collinear,
+// 3 Hirth, 4 glissile junction, 5 Lomer-Cottrell lock
+int interaction_class(int a, int b) {
+  if (a == b) return 0;
+  const int* sa = SL_S[a]; const int* sb = SL_S[b];
+  const int* ma = SL_M[a]; const int* mb = SL_M[b];
+  const int mm = idot(ma, mb);
+  if (mm == 3 || mm == -3) return 1;              // same plane (|m| = sqrt 3)
+  const int ss = idot(sa, sb);                     // |s|^2 = 2
+  if (ss == 2 || ss == -2) return 2;               // same Burgers direction
+  if (ss == 0) return 3;                           // perpendicular Burgers vectors
+  int j[3];
+  const int sg = ss > 0 ? 1 : -1;                  // junction b = b_a - sign(b_a.b_b) b_b
+  for (int k = 0; k < 3; ++k) j[k] = sa[k] - sg * sb[k];
+  return (idot(j, ma) == 0 || idot(j, mb) == 0) ? 4 : 5;
+}
+
+// Gauss-Jordan inverse with partial pivoting (n x n, row-major); false if singular
+bool invert(std::vector<double>& A, int n) {
+  std::vector<double> I(n * n, 0.0);
+  for (int i = 0; i < n; ++i) I[i * n + i] = 1.0;
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::fabs(A[i * n + k]) > std::fabs(A[p * n + k])) p = i;
+    if (A[p * n + k] == 0.0) return false;
+    for (int j = 0; j < n; ++j) { std::swap(A[k * n + j], A[p * n + j]); std::swap(I[k * n + j], I[p * n + j]); }
+    const double d = 1.0 / A[k * n + k];
+    for (int j = 0; j < n; ++j) { A[k * n + j] *= d; I[k * n + j] *= d; }
+    for (int i = 0; i < n; ++i) {
+      if (i == k) continue;
+      const double f = A[i * n + k];
+      if (f == 0.0) continue;
+      for (int j = 0; j < n; ++j) { A[i * n + j] -= f * A[k * n + j]; I[i * n + j] -= f * I[k * n + j]; }
+    }
+  }
+  A = I;
+  return true;
+}
+
+void build_tables(const rve_material& m, std::vector<double>& q, std::vector<double>& Ap, std::vector<int32_t>& screw) {
+  q.assign(144, 0.0);
+  const double norm = m.q_normalise ? m.q[0] : 1.0;
+  for (int a = 0; a < 12; ++a)
+    for (int b = 0; b < 12; ++b) q[12 * a + b] = m.q[interaction_class(a, b)] / norm;
+  // A (9 x 18), crystal frame, unit b and t: columns = vec(b (x) t)
+  double A[9][18];
+  for (int a = 0; a < 18; ++a) {
+    double bv[3], tv[3];
+    if (a < 12) {
+      const double is2 = 1.0 / std::sqrt(2.0), is3 = 1.0 / std::sqrt(3.0);
+      double s[3], mm[3];
+      for (int k = 0; k < 3; ++k) { s[k] = SL_S[a][k] * is2; mm[k] = SL_M[a][k] * is3; }
+      for (int k = 0; k < 3; ++k) bv[k] = s[k];
+      tv[0] = mm[1] * s[2] - mm[2] * s[1];   // t = m x s
+      tv[1] = mm[2] * s[0] - mm[0] * s[2];
+      tv[2] = mm[0] * s[1] - mm[1] * s[0];
+    } else {
+      const double is2 = 1.0 / std::sqrt(2.0);
+      for (int k = 0; k < 3; ++k) bv[k] = tv[k] = SCREW[a - 12][k] * is2;
+    }
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) A[3 * i + j][a] = bv[i] * tv[j];
+  }
+  std::vector<double> AAt(81, 0.0);
+  for (int i = 0; i < 9; ++i)
+    for (int j = 0; j < 9; ++j) {
+      double s = 0.0;
+      for (int a = 0; a < 18; ++a) s += A[i][a] * A[j][a];
+      AAt[9 * i + j] = s;
+    }
+  invert(AAt, 9);
+  Ap.assign(162, 0.0);   // A^T (A A^T)^-1 / b
+  for (int a = 0; a < 18; ++a)
+    for (int j = 0; j < 9; ++j) {
+      double s = 0.0;
+      for (int i = 0; i < 9; ++i) s += A[i][a] * AAt[9 * i + j];
+      Ap[9 * a + j] = s / m.b;
+    }
+  screw.assign(12, 0);
+  for (int a = 0; a < 12; ++a)
+    for (int d = 0; d < 6; ++d) {
+      const int v = idot(SL_S[a], SCREW[d]);
+      if (v == 2 || v == -2) screw[a] = d;
+    }
+}
+
+void quat_to_R(const double* qin, double* R) {
+  double w = qin[0], x = qin[1], y = qin[2], z = qin[3];
+  const double n = std::sqrt(w * w + x * x + y * y + z * z);
+  w /= n; x /= n; y /= n; z /= n;
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
+}
+
+rve_status read_scalars(rve_s* h) {
+  RVE_CUDA(h, cudaMemcpyAsync(h->hscal, h->dscal, 64 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  RVE_CUDA(h, cudaMemcpyAsync(h->hcount, h->dcount, 16 * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  RVE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return RVE_OK;
+}
+
+rve_status read_rr(rve_s* h, double* rr) {
+  RVE_CUDA(h, cudaMemcpyAsync(h->hscal + DS_RR, h->dscal + DS_RR, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  RVE_CUDA(h, cudaStreamSynchronize(h->stream));
+  *rr = h->hscal[DS_RR];
+  return RVE_OK;
+}
+
+SpecParams project_params(const rve_s* h, const uint8_t* mask, const double* shift, double* mean_out) {
+  SpecParams sp;
+  sp.op = OP_PROJECT;
+  for (int c = 0; c < 9; ++c) {
+    sp.keep[c] = mask[c] ? 0 : 1;
+    sp.shift[c] = shift ? shift[c] : 0.0;
+  }
+  sp.inv_nvox = 1.0 / (double)h->nvox;
+  sp.inv4h = 0.25 / h->h;
+  sp.mean_out = mean_out;
+  return sp;
+}
+
+rve_status run_project(rve_s* h, const double* in, double* out, const SpecParams& sp) {
+  RVE_CUDA(h, launch_fft_forward(h, in, h->stream));
+  RVE_CUDA(h, launch_fft_op(h, sp, h->stream));
+  RVE_CUDA(h, launch_fft_inverse(h, out, h->stream));
+  return RVE_OK;
+}
+
+rve_status run_hardening(rve_s* h) {
+  SpecParams sp = project_params(h, (const uint8_t*)"\0\0\0\0\0\0\0\0\0", nullptr, nullptr);
+  sp.op = OP_CURL;
+  RVE_TRY(run_project(h, h->Fp, h->nye, sp));
+  RVE_CUDA(h, launch_hardening(h, h->stream));
+  return RVE_OK;
+}
+
+// evaluate the local update at F + lambda x into buffer `out` and the
+// residual R = G*(P - Pbar); returns rms(R) and the mean of P
+rve_status eval_residual(rve_s* h, double dt, double lambda, int out, int warm, const uint8_t* mask,
+                         const double* Pbar_m, double* rabs, double* scale, int* lmax, int* lfail) {
+  RVE_CUDA(h, cudaMemsetAsync(h->dcount, 0, 2 * sizeof(int32_t), h->stream));
+  RVE_CUDA(h, launch_constitutive(h, dt, lambda, out, warm, h->stream));
+  SpecParams sp = project_params(h, mask, Pbar_m, h->dscal + DS_MEANP);
+  RVE_TRY(run_project(h, h->P[out], h->R, sp));
+  RVE_CUDA(h, launch_norm2(h, h->R, 9, h->stream));
+  RVE_TRY(read_scalars(h));
+  *rabs = std::sqrt(h->hscal[DS_NORM] / (double)h->nvox);
+  double pn = 0.0;
+  for (int c = 0; c < 9; ++c) pn += h->hscal[DS_MEANP + c] * h->hscal[DS_MEANP + c];
+  *scale = std::fmax(std::sqrt(pn), 1e-4 * h->mu);
+  *lmax = h->hcount[0];
+  *lfail = h->hcount[1];
+  return RVE_OK;
+}
+
+// CG on G*(K : x) = -R from x = 0; returns the iteration count
+rve_status cg_solve(rve_s* h, const uint8_t* mask, int* iters, bool* ok) {
+  RVE_CUDA(h, launch_cg_init(h, h->stream));
+  double rr;
+  RVE_TRY(read_rr(h, &rr));
+  const double stop = h->opt.cg_tol * h->opt.cg_tol * rr;
+  SpecParams sp = project_params(h, mask, nullptr, nullptr);
+  int k = 0;
+  *ok = false;
+  for (; k < h->opt.max_cg; ++k) {
+    if (rr <= stop) { *ok = true; break; }
+    RVE_CUDA(h, launch_tangent_apply(h, k == 0, h->stream));
+    RVE_TRY(run_project(h, h->t, h->q, sp));
+    RVE_CUDA(h, launch_cg_update(h, h->stream));
+    RVE_TRY(read_rr(h, &rr));
+    if (!std::isfinite(rr)) break;
+  }
+  if (!*ok && rr <= stop) *ok = true;
+  *iters = k;
+  return RVE_OK;
+}
+
+rve_status fail(rve_s* h, rve_status s, const char* msg) {
+  h->err = msg;
+  return s;
+}
+
+int ncomp_of(uint32_t which) {
+  switch (which) {
+    case RVE_FIELD_F: case RVE_FIELD_P: case RVE_FIELD_FP: case RVE_FIELD_SIGMA: case RVE_FIELD_NYE:
+    case RVE_FIELD_P_EVAL: return 9;
+    case RVE_FIELD_S: case RVE_FIELD_S_EVAL: return 6;
+    case RVE_FIELD_RHO_SSD: case RVE_FIELD_RHO_GND: case RVE_FIELD_TAUC: case RVE_FIELD_DGAM: return 12;
+    case RVE_FIELD_RHO_GND18: return 18;
+    case RVE_FIELD_VM: case RVE_FIELD_GRAIN: return 1;
+    case RVE_FIELD_TANGENT: return 81;
+    default: return 0;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t rve_workspace_bytes(int n0, int n1, int n2, int n_grains, int precision) {
+  if (precision != 0 || n_grains < 1) return 0;
+  if (!good_len(n0, 2) || !good_len(n1, 2) || !good_len(n2, 1) || (n0 & 1) || (n1 & 1)) return 0;
+  rve_s h;
+  h.n0 = n0; h.n1 = n1; h.n2 = n2; h.nkx = n0 / 2 + 1;
+  h.nvox = (size_t)n0 * n1 * n2;
+  h.nspec = (size_t)h.nkx * n1 * n2;
+  h.ngrains = n_grains;
+  Carver c{nullptr};
+  carve(&h, c);
+  return c.off;
+}
+
+rve_status rve_create(const int32_t* grain_id, int n0, int n1, int n2, const double* quat, int n_grains,
+                      const rve_material* mat, const rve_options* opt, void* d_workspace, size_t ws_bytes,
+                      void* cuda_stream, rve_t** out) {
+  if (!out) return RVE_EINVAL;
+  *out = nullptr;
+  if (!grain_id || !quat || !mat || !opt || !d_workspace) return RVE_EINVAL;
+  const size_t need = rve_workspace_bytes(n0, n1, n2, n_grains, opt->precision);
+  if (need == 0) return RVE_EINVAL;
+  if (ws_bytes < need) return RVE_ENOMEM;
+  if (reinterpret_cast<uintptr_t>(d_workspace) & 255) return RVE_EINVAL;
+  if (!(mat->C11 > 0 && mat->C44 > 0 && mat->C11 > mat->C12 && mat->b > 0 && mat->gdot0 > 0 && mat->n >= 1 &&
+        mat->K > 0 && mat->yc >= 0 && mat->rho0_total > 0 && mat->tau0 >= 0 && mat->alpha >= 0 &&
+        mat->q[0] > 0 && opt->L > 0 && opt->newton_tol > 0 && opt->cg_tol > 0 && opt->local_tol > 0 &&
+        opt->max_newton > 0 && opt->max_cg > 0 && opt->max_local > 0 && opt->max_halvings >= 0))
+    return RVE_EINVAL;
+  const size_t nvox = (size_t)n0 * n1 * n2;
+  for (size_t v = 0; v < nvox; ++v)
+    if (grain_id[v] < 0 || grain_id[v] >= n_grains) return RVE_EINVAL;
+  for (int g = 0; g < n_grains; ++g) {
+    const double* qq = quat + 4 * g;
+    const double nn = qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2] + qq[3] * qq[3];
+    if (!(nn > 0) || !std::isfinite(nn)) return RVE_EINVAL;
+  }
+
+  rve_s* h = new (std::nothrow) rve_s();
+  if (!h) return RVE_ENOMEM;
+  h->n0 = n0; h->n1 = n1; h->n2 = n2; h->nkx = n0 / 2 + 1;
+  h->nvox = nvox;
+  h->nspec = (size_t)h->nkx * n1 * n2;
+  h->ngrains = n_grains;
+  h->mat = *mat;
+  h->opt = *opt;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->h = opt->L / n0;
+  h->mu = mat->mu > 0 ? mat->mu : 3.0 * mat->C44 * (mat->C11 - mat->C12) / (4.0 * mat->C44 + mat->C11 - mat->C12);
+  h->cur = 0;
+  h->increment = 0;
+  h->dt_prev = 1.0;
+  for (int c = 0; c < 9; ++c) { h->dFbar_prev[c] = 0.0; h->Pmacro[c] = 0.0; h->Smacro[c] = 0.0; }
+  make_plan(n0, &h->plan[0]);
+  make_plan(n1, &h->plan[1]);
+  make_plan(n2, &h->plan[2]);
+  Consts& c = h->cst;
+  c.C11 = mat->C11; c.C12 = mat->C12; c.C44 = mat->C44; c.mu = h->mu; c.b = mat->b;
+  c.tau0 = mat->tau0; c.alpha = mat->alpha; c.gdot0 = mat->gdot0; c.n = mat->n; c.K = mat->K; c.yc = mat->yc;
+  c.n_int = (mat->n == std::floor(mat->n) && mat->n >= 1 && mat->n <= 64) ? (int)mat->n : 0;
+  c.gnd_enabled = mat->gnd_enabled ? 1 : 0;
+  c.local_tol_abs = opt->local_tol * h->mu;
+  c.floor_abs = 10.0 * c.local_tol_abs;
+  c.dgam_max = 0.1;
+  c.max_local = opt->max_local;
+  c.max_halvings = 40;
+
+  Carver cv{static_cast<char*>(d_workspace)};
+  carve(h, cv);
+  if (cudaMallocHost((void**)&h->hscal, 64 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost((void**)&h->hcount, 16 * sizeof(int32_t)) != cudaSuccess) {
+    delete h;
+    return RVE_ECUDA;
+  }
+  auto bad = [&](cudaError_t e) {
+    if (e == cudaSuccess) return false;
+    h->err = cudaGetErrorString(e);
+    return true;
+  };
+  // tables
+  std::vector<double> R(9 * (size_t)n_grains), q, Ap;
+  std::vector<int32_t> screw;
+  for (int g = 0; g < n_grains; ++g) quat_to_R(quat + 4 * g, &R[9 * g]);
+  build_tables(*mat, q, Ap, screw);
+  const int ns[3] = {n0, n1, n2};
+  std::vector<double2> tw[3], ph[3];
+  std::vector<double> tn[3];
+  std::vector<int8_t> nq[3];
+  const double PI = 3.14159265358979323846;
+  for (int a = 0; a < 3; ++a) {
+    const int n = ns[a];
+    tw[a].resize(n); ph[a].resize(n); tn[a].resize(n); nq[a].resize(n);
+    for (int t = 0; t < n; ++t) {
+      const double ang = 2.0 * PI * (double)t / n;
+      tw[a][t] = make_double2(std::cos(ang), -std::sin(ang));
+      const bool nyq = (2 * t == n);
+      const int ks = (2 * t <= n) ? t : t - n;
+      nq[a][t] = nyq ? 1 : 0;
+      tn[a][t] = nyq ? 0.0 : std::tan(PI * (double)ks / n);
+      ph[a][t] = nyq ? make_double2(-1.0, 0.0) : make_double2(std::cos(ang), std::sin(ang));
+    }
+    // exact values at the quarter points
+    for (int t = 0; t < n; ++t) {
+      if (4 * t == n) { tw[a][t] = make_double2(0.0, -1.0); ph[a][t] = make_double2(0.0, 1.0); }
+      if (4 * t == 3 * n) { tw[a][t] = make_double2(0.0, 1.0); ph[a][t] = make_double2(0.0, -1.0); }
+      if (2 * t == n) tw[a][t] = make_double2(-1.0, 0.0);
+    }
+    tw[a][0] = make_double2(1.0, 0.0);
+    ph[a][0] = make_double2(1.0, 0.0);
+  }
+  cudaStream_t s = h->stream;
+  bool fail_ = bad(cudaMemcpyAsync(h->grain, grain_id, nvox * sizeof(int32_t), cudaMemcpyHostToDevice, s)) ||
+               bad(cudaMemcpyAsync(h->grainR, R.data(), R.size() * sizeof(double), cudaMemcpyHostToDevice, s)) ||
+               bad(cudaMemcpyAsync(h->qhat, q.data(), 144 * sizeof(double), cudaMemcpyHostToDevice, s)) ||
+               bad(cudaMemcpyAsync(h->Apinv, Ap.data(), 162 * sizeof(double), cudaMemcpyHostToDevice, s)) ||
+               bad(cudaMemcpyAsync(h->screw_of, screw.data(), 12 * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  for (int a = 0; a < 3 && !fail_; ++a) {
+    fail_ = bad(cudaMemcpyAsync((void*)h->ax[a].tw, tw[a].data(), ns[a] * sizeof(double2), cudaMemcpyHostToDevice, s)) ||
+            bad(cudaMemcpyAsync((void*)h->ax[a].tanh_, tn[a].data(), ns[a] * sizeof(double), cudaMemcpyHostToDevice, s)) ||
+            bad(cudaMemcpyAsync((void*)h->ax[a].nyq, nq[a].data(), ns[a] * sizeof(int8_t), cudaMemcpyHostToDevice, s)) ||
+            bad(cudaMemcpyAsync((void*)h->ax[a].ph, ph[a].data(), ns[a] * sizeof(double2), cudaMemcpyHostToDevice, s));
+  }
+  // initial state: F = Fp = I, S = 0, rho_SSD = rho0 / 12, dF_last = 0
+  if (!fail_) {
+    std::vector<double> ident(9 * nvox, 0.0), rho(12 * nvox, mat->rho0_total / 12.0);
+    for (int k = 0; k < 9; k += 4)
+      for (size_t v = 0; v < nvox; ++v) ident[k * nvox + v] = 1.0;
+    fail_ = bad(cudaMemcpyAsync(h->F_c, ident.data(), 9 * nvox * sizeof(double), cudaMemcpyHostToDevice, s)) ||
+            bad(cudaMemcpyAsync(h->Fp, ident.data(), 9 * nvox * sizeof(double), cudaMemcpyHostToDevice, s)) ||
+            bad(cudaMemcpyAsync(h->F, ident.data(), 9 * nvox * sizeof(double), cudaMemcpyHostToDevice, s)) ||
+            bad(cudaMemcpyAsync(h->rho_ssd, rho.data(), 12 * nvox * sizeof(double), cudaMemcpyHostToDevice, s)) ||
+            bad(cudaMemsetAsync(h->S_c, 0, 6 * nvox * sizeof(double), s)) ||
+            bad(cudaMemsetAsync(h->S[0], 0, 6 * nvox * sizeof(double), s)) ||
+            bad(cudaMemsetAsync(h->S[1], 0, 6 * nvox * sizeof(double), s)) ||
+            bad(cudaMemsetAsync(h->P_c, 0, 9 * nvox * sizeof(double), s)) ||
+            bad(cudaMemsetAsync(h->P[0], 0, 9 * nvox * sizeof(double), s)) ||
+            bad(cudaMemsetAsync(h->dF_last, 0, 9 * nvox * sizeof(double), s)) ||
+            bad(cudaMemsetAsync(h->nye, 0, 9 * nvox * sizeof(double), s)) ||
+            bad(cudaMemsetAsync(h->dscal, 0, 64 * sizeof(double), s)) ||
+            bad(cudaStreamSynchronize(s));
+  }
+  if (fail_) {
+    cudaFreeHost(h->hscal);
+    cudaFreeHost(h->hcount);
+    delete h;
+    return RVE_ECUDA;
+  }
+  *out = h;
+  return RVE_OK;
+}
+
+rve_status rve_step(rve_t* h, const double dFbar[9], const uint8_t strain_mask[9], const double Pbar[9], double dt,
+                    rve_step_info* info) {
+  if (!h || !dFbar || !strain_mask || !Pbar || !(dt > 0) || !std::isfinite(dt)) return RVE_EINVAL;
+  for (int c = 0; c < 9; ++c)
+    if (!std::isfinite(dFbar[c]) || !std::isfinite(Pbar[c])) return fail(h, RVE_EINVAL, "non-finite load");
+  const auto t0 = std::chrono::steady_clock::now();
+  rve_step_info loc;
+  std::memset(&loc, 0, sizeof(loc));
+  uint8_t mask[9];
+  double dFb[9], Pb[9];
+  for (int c = 0; c < 9; ++c) {
+    mask[c] = strain_mask[c] ? 1 : 0;
+    dFb[c] = mask[c] ? dFbar[c] : 0.0;
+    Pb[c] = mask[c] ? 0.0 : Pbar[c];
+  }
+  auto finish = [&](rve_status st) {
+    loc.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = loc;
+    return st;
+  };
+  rve_status st = run_hardening(h);
+  if (st != RVE_OK) return finish(st);
+  const int extrap = (h->opt.extrapolate && h->increment > 0) ? 1 : 0;
+  const double ratio = dt / h->dt_prev;
+  if (cudaError_t e = launch_predictor(h, dFb, h->dFbar_prev, ratio, extrap, h->stream)) {
+    h->err = cudaGetErrorString(e);
+    return finish(RVE_ECUDA);
+  }
+  int cur = 0;
+  double rabs, scale;
+  int lmax, lfail;
+  h->cur = cur;
+  st = eval_residual(h, dt, 0.0, cur, -1, mask, Pb, &rabs, &scale, &lmax, &lfail);
+  if (st != RVE_OK) return finish(st);
+  loc.local_max_iters = lmax;
+  loc.local_failures = lfail;
+  double res = rabs / scale;
+  loc.residuals[0] = res;
+  for (;;) {
+    loc.residual = res;
+    if (lfail) return finish(fail(h, RVE_ENOCONV_LOCAL, "local update did not converge"));
+    if (!std::isfinite(res)) return finish(fail(h, RVE_ENAN, "non-finite residual"));
+    if (res <= h->opt.newton_tol) break;
+    if (loc.newton_iters >= h->opt.max_newton)
+      return finish(fail(h, RVE_ENOCONV_NEWTON, "Newton-Raphson reached max_newton"));
+    int ncg;
+    bool cgok;
+    st = cg_solve(h, mask, &ncg, &cgok);
+    if (st != RVE_OK) return finish(st);
+    if (loc.newton_iters < RVE_MAX_NEWTON_LOG) loc.cg_iters[loc.newton_iters] = ncg;
+    loc.cg_iters_total += ncg;
+    double lam = 1.0, rt = 0.0, sct = 0.0;
+    int lm = 0, lf = 0;
+    bool acc = false;
+    for (int hv = 0; hv <= h->opt.max_halvings; ++hv) {
+      st = eval_residual(h, dt, lam, 1 - cur, cur, mask, Pb, &rt, &sct, &lm, &lf);
+      if (st != RVE_OK) return finish(st);
+      if (lf == 0 && rt < rabs) { acc = true; break; }
+      lam *= 0.5;
+      ++loc.halvings;
+    }
+    if (!acc) {
+      if (lf) return finish(fail(h, RVE_ENOCONV_LOCAL, "local update did not converge in the line search"));
+      return finish(fail(h, RVE_ENOCONV_NEWTON, "no step along the Newton direction lowers the residual"));
+    }
+    if (cudaError_t e = launch_axpy_F(h, lam, h->stream)) {
+      h->err = cudaGetErrorString(e);
+      return finish(RVE_ECUDA);
+    }
+    cur = 1 - cur;
+    h->cur = cur;
+    rabs = rt;
+    res = rt / sct;
+    loc.local_max_iters = lm > loc.local_max_iters ? lm : loc.local_max_iters;
+    ++loc.newton_iters;
+    if (loc.newton_iters <= RVE_MAX_NEWTON_LOG) loc.residuals[loc.newton_iters] = res;
+  }
+  loc.converged = 1;
+  if (cudaError_t e = launch_commit(h, h->stream)) {
+    h->err = cudaGetErrorString(e);
+    return finish(RVE_ECUDA);
+  }
+  if (cudaError_t e = launch_macro(h, h->stream)) {
+    h->err = cudaGetErrorString(e);
+    return finish(RVE_ECUDA);
+  }
+  st = read_scalars(h);
+  if (st != RVE_OK) return finish(st);
+  for (int c = 0; c < 9; ++c) {
+    h->Pmacro[c] = h->hscal[DS_MEANP + c] / (double)h->nvox;
+    h->Smacro[c] = h->hscal[DS_MEANSIG + c] / (double)h->nvox;
+    h->dFbar_prev[c] = dFb[c];
+  }
+  h->dt_prev = dt;
+  ++h->increment;
+  return finish(RVE_OK);
+}
+
+rve_status rve_get_macro_stress(rve_t* h, double P[9], double sigma[9]) {
+  if (!h || !P || !sigma) return RVE_EINVAL;
+  for (int c = 0; c < 9; ++c) { P[c] = h->Pmacro[c]; sigma[c] = h->Smacro[c]; }
+  return RVE_OK;
+}
+
+rve_status rve_get_fields(rve_t* h, uint32_t which, void* dst, size_t bytes, int dst_is_device) {
+  if (!h || !dst) return RVE_EINVAL;
+  const int nc = ncomp_of(which);
+  if (nc == 0) return fail(h, RVE_EINVAL, "unknown field selector");
+  const size_t esz = which == RVE_FIELD_GRAIN ? sizeof(int32_t) : sizeof(double);
+  const size_t need = (size_t)nc * h->nvox * esz;
+  if (bytes < need) return fail(h, RVE_EINVAL, "destination too small");
+  const void* src = nullptr;
+  switch (which) {
+    case RVE_FIELD_F: src = h->F_c; break;
+    case RVE_FIELD_P: src = h->P_c; break;
+    case RVE_FIELD_FP: src = h->Fp; break;
+    case RVE_FIELD_RHO_SSD: src = h->rho_ssd; break;
+    case RVE_FIELD_RHO_GND: src = h->rho_gnd; break;
+    case RVE_FIELD_RHO_GND18: src = h->rho18; break;
+    case RVE_FIELD_NYE: src = h->nye; break;
+    case RVE_FIELD_TAUC: src = h->tauc; break;
+    case RVE_FIELD_DGAM: src = h->dgam[h->cur]; break;
+    case RVE_FIELD_TANGENT: src = h->K[h->cur]; break;
+    case RVE_FIELD_GRAIN: src = h->grain; break;
+    case RVE_FIELD_P_EVAL: src = h->P[h->cur]; break;
+    case RVE_FIELD_SIGMA:
+      RVE_CUDA(h, launch_output_field(h, 0, h->P_c, h->S_c, h->q, h->stream));
+      src = h->q; break;
+    case RVE_FIELD_VM:
+      RVE_CUDA(h, launch_output_field(h, 1, h->P_c, h->S_c, h->q, h->stream));
+      src = h->q; break;
+    case RVE_FIELD_S:
+      RVE_CUDA(h, launch_output_field(h, 2, h->P_c, h->S_c, h->q, h->stream));
+      src = h->q; break;
+    case RVE_FIELD_S_EVAL:
+      RVE_CUDA(h, launch_output_field(h, 2, h->P_c, h->S[h->cur], h->q, h->stream));
+      src = h->q; break;
+  }
+  RVE_CUDA(h, cudaMemcpyAsync(dst, src, need, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                              h->stream));
+  RVE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return RVE_OK;
+}
+
+rve_status rve_set_fields(rve_t* h, uint32_t which, const void* src, size_t bytes, int src_is_device) {
+  if (!h || !src) return RVE_EINVAL;
+  double* dst = nullptr;
+  int nc = 0;
+  switch (which) {
+    case RVE_FIELD_F: dst = h->F_c; nc = 9; break;
+    case RVE_FIELD_FP: dst = h->Fp; nc = 9; break;
+    case RVE_FIELD_RHO_SSD: dst = h->rho_ssd; nc = 12; break;
+    default: return fail(h, RVE_EINVAL, "field cannot be set");
+  }
+  if (bytes != (size_t)nc * h->nvox * sizeof(double)) return fail(h, RVE_EINVAL, "wrong byte count");
+  RVE_CUDA(h, cudaMemcpyAsync(dst, src, bytes, src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              h->stream));
+  RVE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return RVE_OK;
+}
+
+rve_status rve_eval_hardening(rve_t* h) {
+  if (!h) return RVE_EINVAL;
+  RVE_TRY(run_hardening(h));
+  RVE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return RVE_OK;
+}
+
+rve_status rve_eval_constitutive(rve_t* h, double dt, int32_t* local_max_iters, int32_t* local_failures) {
+  if (!h || !(dt > 0)) return RVE_EINVAL;
+  RVE_TRY(run_hardening(h));
+  RVE_CUDA(h, cudaMemcpyAsync(h->F, h->F_c, 9 * h->nvox * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  RVE_CUDA(h, cudaMemsetAsync(h->dcount, 0, 2 * sizeof(int32_t), h->stream));
+  RVE_CUDA(h, launch_constitutive(h, dt, 0.0, h->cur, -1, h->stream));
+  RVE_TRY(read_scalars(h));
+  if (local_max_iters) *local_max_iters = h->hcount[0];
+  if (local_failures) *local_failures = h->hcount[1];
+  return RVE_OK;
+}
+
+rve_status rve_project(rve_t* h, const uint8_t strain_mask[9], const double* d_X, double* d_Y) {
+  if (!h || !strain_mask || !d_X || !d_Y) return RVE_EINVAL;
+  SpecParams sp = project_params(h, strain_mask, nullptr, nullptr);
+  RVE_TRY(run_project(h, d_X, d_Y, sp));
+  RVE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return RVE_OK;
+}
+
+struct CkptHeader {
+  uint32_t magic, version;
+  int32_t n0, n1, n2, ngrains, increment, cur;
+  double dt_prev;
+  double dFbar_prev[9], Pmacro[9], Smacro[9];
+};
+
+size_t rve_checkpoint_bytes(const rve_t* h) {
+  if (!h) return 0;
+  return sizeof(CkptHeader) + (size_t)(9 + 9 + 6 + 12 + 9 + 9) * h->nvox * sizeof(double);
+}
+
+rve_status rve_checkpoint(rve_t* h, void* host_buf, size_t bytes) {
+  if (!h || !host_buf || bytes < rve_checkpoint_bytes(h)) return RVE_EINVAL;
+  CkptHeader hd;
+  hd.magic = CKPT_MAGIC; hd.version = CKPT_VERSION;
+  hd.n0 = h->n0; hd.n1 = h->n1; hd.n2 = h->n2; hd.ngrains = h->ngrains;
+  hd.increment = h->increment; hd.cur = 0; hd.dt_prev = h->dt_prev;
+  for (int c = 0; c < 9; ++c) { hd.dFbar_prev[c] = h->dFbar_prev[c]; hd.Pmacro[c] = h->Pmacro[c]; hd.Smacro[c] = h->Smacro[c]; }
+  char* p = static_cast<char*>(host_buf);
+  std::memcpy(p, &hd, sizeof(hd));
+  p += sizeof(hd);
+  const double* bufs[6] = {h->F_c, h->Fp, h->S_c, h->rho_ssd, h->dF_last, h->P_c};
+  const int nc[6] = {9, 9, 6, 12, 9, 9};
+  for (int b = 0; b < 6; ++b) {
+    const size_t n = (size_t)nc[b] * h->nvox * sizeof(double);
+    RVE_CUDA(h, cudaMemcpyAsync(p, bufs[b], n, cudaMemcpyDeviceToHost, h->stream));
+    p += n;
+  }
+  RVE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return RVE_OK;
+}
+
+rve_status rve_restore(rve_t* h, const void* host_buf, size_t bytes) {
+  if (!h || !host_buf || bytes < rve_checkpoint_bytes(h)) return RVE_EINVAL;
+  CkptHeader hd;
+  std::memcpy(&hd, host_buf, sizeof(hd));
+  if (hd.magic != CKPT_MAGIC || hd.version != CKPT_VERSION || hd.n0 != h->n0 || hd.n1 != h->n1 || hd.n2 != h->n2 ||
+      hd.ngrains != h->ngrains || !(hd.dt_prev > 0) || hd.increment < 0)
+    return fail(h, RVE_EINVAL, "checkpoint does not match this handle");
+  const char* p = static_cast<const char*>(host_buf) + sizeof(hd);
+  double* bufs[6] = {h->F_c, h->Fp, h->S_c, h->rho_ssd, h->dF_last, h->P_c};
+  const int nc[6] = {9, 9, 6, 12, 9, 9};
+  for (int b = 0; b < 6; ++b) {
+    const size_t n = (size_t)nc[b] * h->nvox * sizeof(double);
+    RVE_CUDA(h, cudaMemcpyAsync(bufs[b], p, n, cudaMemcpyHostToDevice, h->stream));
+    p += n;
+  }
+  RVE_CUDA(h, cudaMemcpyAsync(h->S[0], h->S_c, 6 * h->nvox * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  RVE_CUDA(h, cudaMemcpyAsync(h->P[0], h->P_c, 9 * h->nvox * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  RVE_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->cur = 0;
+  h->increment = hd.increment;
+  h->dt_prev = hd.dt_prev;
+  for (int c = 0; c < 9; ++c) { h->dFbar_prev[c] = hd.dFbar_prev[c]; h->Pmacro[c] = hd.Pmacro[c]; h->Smacro[c] = hd.Smacro[c]; }
+  return RVE_OK;
+}
+
+const char* rve_last_error(const rve_t* h) { return h ? h->err.c_str() : "null handle"; }
+
+void rve_destroy(rve_t* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  cudaFreeHost(h->hscal);
+  cudaFreeHost(h->hcount);
+  delete h;
+}
+
+}  // extern "C"

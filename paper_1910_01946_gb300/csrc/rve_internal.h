@@ -1,0 +1,117 @@
+// Internal declarations of the GB300 path: the handle, the per-handle device
+// tables and the launch wrappers of every kernel (defined in fft.cu,
+// constitutive.cu and vec.cu; orchestrated by rve_api.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/rve.h"
+
+#define RVE_MAX_RADIX_PASSES 12
+#define RVE_RED_BLOCKS 1216      // 152 SMs x 8: grid of the reducing kernels
+#define RVE_RED_THREADS 256
+
+struct FFTPlan {
+  int n;                                  // transform length
+  int npass;                              // number of radix passes
+  int radix[RVE_MAX_RADIX_PASSES];
+};
+
+// Operator applied in frequency space between the forward and inverse z passes.
+enum SpecOp { OP_PROJECT = 0, OP_CURL = 1 };
+
+struct SpecParams {
+  int op;
+  int keep[9];          // zero mode: 1 = keep (stress-controlled) component
+  double shift[9];      // zero mode: subtract nvox * shift[c] (the prescribed Pbar)
+  double inv_nvox;
+  double inv4h;         // 1 / (4 h) for the curl
+  double* mean_out;     // nullable: receives X^(0) / nvox (9 doubles) before the shift
+};
+
+// Device tables per axis (in the workspace).
+struct AxisTables {
+  const double2* tw;    // e^{-2 pi i t / n}, t = 0..n-1
+  const double* tanh_;  // tan(pi k' / n) for the frequency index k (signed k'), Nyquist: 0
+  const int8_t* nyq;    // 1 at the Nyquist index of an even n
+  const double2* ph;    // e^{i xi_k}, exactly -1 at Nyquist
+};
+
+struct Consts {        // material constants read by the hardening and constitutive kernels
+  double C11, C12, C44, mu, b, tau0, alpha, gdot0, n, K, yc;
+  int n_int;            // n if it is a positive integer <= 64, else 0 (use pow)
+  int gnd_enabled;
+  double local_tol_abs, floor_abs, dgam_max;
+  int max_local, max_halvings;
+};
+
+struct rve_s {
+  int n0, n1, n2, nkx;
+  size_t nvox, nspec;   // nspec = nkx * n1 * n2
+  int ngrains;
+  rve_material mat;
+  rve_options opt;
+  double mu, h;
+  Consts cst;
+  cudaStream_t stream;
+  FFTPlan plan[3];
+  AxisTables ax[3];
+
+  // device state (all carved from the caller's workspace)
+  int32_t* grain;       // nvox
+  double* grainR;       // 9 * ngrains (crystal -> sample)
+  double* qhat;         // 144 interaction matrix (row-major alpha, beta)
+  double* Apinv;        // 162: A^+ (18 x 9, crystal frame, divided by b)
+  int32_t* screw_of;    // 12
+  double *F_c, *Fp, *S_c, *rho_ssd, *dF_last, *P_c;  // committed
+  double *nye, *rho18, *rho_gnd, *tauc, *ell, *Fp0inv;  // per increment
+  double* F;            // Newton iterate
+  double *P[2], *K[2], *S[2], *dgam[2];             // evaluation double buffer
+  int cur;
+  double *R, *x, *r, *p, *t, *q;
+  double2* spec;        // 9 * nspec
+  double* partial;      // 4 * RVE_RED_BLOCKS
+  double* dscal;        // device scalars (see DS_*)
+  int32_t* dcount;      // device counters: [0] local max iters, [1] local failures
+  double* hscal;        // pinned host mirror of dscal
+  int32_t* hcount;      // pinned host mirror of dcount
+
+  // host-side history
+  double Pmacro[9], Smacro[9];
+  double dFbar_prev[9];
+  double dt_prev;
+  int increment;
+  std::string err;
+};
+
+// device scalar slots
+enum { DS_RR = 0, DS_PKP = 1, DS_ALPHA = 2, DS_BETA = 3, DS_NORM = 4, DS_MEANP = 8,
+       DS_MEANSIG = 17, DS_MEANF = 26, DS_COUNT = 40 };
+
+// ---- fft.cu ----
+cudaError_t launch_fft_forward(const rve_s* h, const double* in, cudaStream_t s);
+cudaError_t launch_fft_op(const rve_s* h, const SpecParams& sp, cudaStream_t s);
+cudaError_t launch_fft_inverse(const rve_s* h, double* out, cudaStream_t s);
+void make_plan(int n, FFTPlan* p);
+
+// ---- constitutive.cu ----
+cudaError_t launch_hardening(const rve_s* h, cudaStream_t s);
+cudaError_t launch_constitutive(const rve_s* h, double dt, double lambda, int out_buf, int warm_buf,
+                                cudaStream_t s);
+
+// ---- vec.cu ----
+cudaError_t launch_tangent_apply(const rve_s* h, int first, cudaStream_t s);
+cudaError_t launch_cg_update(const rve_s* h, cudaStream_t s);
+cudaError_t launch_norm2(const rve_s* h, const double* a, int ncomp, cudaStream_t s);
+cudaError_t launch_reduce_final(const rve_s* h, int mode, cudaStream_t s);
+cudaError_t launch_cg_init(const rve_s* h, cudaStream_t s);
+cudaError_t launch_axpy_F(const rve_s* h, double lambda, cudaStream_t s);
+cudaError_t launch_predictor(const rve_s* h, const double* dFb, const double* dFb_prev, double ratio,
+                             int extrapolate, cudaStream_t s);
+cudaError_t launch_commit(const rve_s* h, cudaStream_t s);
+cudaError_t launch_macro(const rve_s* h, cudaStream_t s);
+cudaError_t launch_output_field(const rve_s* h, int which, const double* P, const double* S, double* dst,
+                               cudaStream_t s);
+
+enum { RED_PKP_ALPHA = 0, RED_RR_BETA = 1, RED_NORM = 2, RED_RR_INIT = 3, RED_MACRO = 4 };

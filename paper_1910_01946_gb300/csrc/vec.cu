@@ -1,0 +1,334 @@
+// Vector kernels of the Newton / conjugate-gradient solve (Sec. 2.2,
+// Eq. linequil2ast), the increment predictor, the commit of the internal
+// variables (Kocks-Mecking SSD update, Eq. kocks, integrated implicitly over
+// the increment) and the volume averages.  All reductions are deterministic:
+// a fixed grid writes one partial per block, a single block sums the
+// partials in a fixed order and derives the CG scalars on the device.
+#include "common.cuh"
+#include "rve_internal.h"
+
+namespace {
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int w = 0; w < nw; ++w) s += sh[w];
+  }
+  __syncthreads();
+  return s;
+}
+
+// p = r (first) or r + beta p; t = K : p; partial of p . t
+__global__ void __launch_bounds__(RVE_RED_THREADS) k_tangent_apply(size_t nvox, const double* __restrict__ K,
+                                                                   const double* __restrict__ r, double* __restrict__ p,
+                                                                   double* __restrict__ t, const double* __restrict__ ds,
+                                                                   int first, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const double beta = first ? 0.0 : ds[DS_BETA];
+  double acc = 0.0;
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (size_t)gridDim.x * blockDim.x) {
+    double pv[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const double rv = r[k * nvox + v];
+      pv[k] = first ? rv : fma(beta, p[k * nvox + v], rv);
+      p[k * nvox + v] = pv[k];
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      double s = 0.0;
+#pragma unroll
+      for (int j = 0; j < 9; ++j) s = fma(K[(size_t)(9 * i + j) * nvox + v], pv[j], s);
+      t[i * nvox + v] = s;
+      acc = fma(pv[i], s, acc);
+    }
+  }
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// x += alpha p; r -= alpha q; partial of r . r
+__global__ void __launch_bounds__(RVE_RED_THREADS) k_cg_update(size_t n, double* __restrict__ x, double* __restrict__ r,
+                                                               const double* __restrict__ p, const double* __restrict__ q,
+                                                               const double* __restrict__ ds, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const double alpha = ds[DS_ALPHA];
+  double acc = 0.0;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    x[e] = fma(alpha, p[e], x[e]);
+    const double rv = fma(-alpha, q[e], r[e]);
+    r[e] = rv;
+    acc = fma(rv, rv, acc);
+  }
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// x = 0; r = -R; partial of r . r
+__global__ void __launch_bounds__(RVE_RED_THREADS) k_cg_init(size_t n, double* __restrict__ x, double* __restrict__ r,
+                                                             const double* __restrict__ R, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    x[e] = 0.0;
+    const double rv = -R[e];
+    r[e] = rv;
+    acc = fma(rv, rv, acc);
+  }
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(RVE_RED_THREADS) k_norm2(size_t n, const double* __restrict__ a, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    acc = fma(a[e], a[e], acc);
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(1024) k_reduce_final(const double* __restrict__ partial, int nparts, int nval,
+                                                       int mode, double* __restrict__ ds) {
+  __shared__ double sh[32];
+  for (int c = 0; c < nval; ++c) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += partial[(size_t)c * nparts + i];
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) {
+      if (mode == RED_PKP_ALPHA) {
+        ds[DS_PKP] = s;
+        ds[DS_ALPHA] = ds[DS_RR] / s;
+      } else if (mode == RED_RR_BETA) {
+        ds[DS_BETA] = s / ds[DS_RR];
+        ds[DS_RR] = s;
+      } else if (mode == RED_RR_INIT) {
+        ds[DS_RR] = s;
+      } else if (mode == RED_NORM) {
+        ds[DS_NORM] = s;
+      } else {  // RED_MACRO: 27 averages -> mean P, mean sigma, mean F
+        ds[DS_MEANP + c] = s;
+      }
+    }
+  }
+}
+
+__global__ void k_axpy(size_t n, double* __restrict__ y, const double* __restrict__ x, double a) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    y[e] = fma(a, x[e], y[e]);
+}
+
+struct Nine { double v[9]; };
+
+__global__ void k_predictor(size_t nvox, double* __restrict__ F, const double* __restrict__ Fc,
+                            const double* __restrict__ dFl, Nine shift, double ratio, int extrapolate) {
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      double f = Fc[k * nvox + v] + shift.v[k];
+      if (extrapolate) f = fma(ratio, dFl[k * nvox + v], f);
+      F[k * nvox + v] = f;
+    }
+  }
+}
+
+// Commit: Fp <- R (I + sum dgam s (x) m) R^T Fp; rho_SSD by implicit Kocks-Mecking;
+// S_c <- S; dF_last <- F - F_c; F_c <- F.
+__global__ void __launch_bounds__(128) k_commit(size_t nvox, const int32_t* __restrict__ grain,
+                                                const double* __restrict__ grainR, const double* __restrict__ dgam,
+                                                const double* __restrict__ S, const double* __restrict__ ell,
+                                                const double* __restrict__ F, double* __restrict__ Fc,
+                                                double* __restrict__ dFl, double* __restrict__ Fp,
+                                                double* __restrict__ Sc, double* __restrict__ rho,
+                                                const double* __restrict__ P, double* __restrict__ Pc, double b, double yc) {
+  const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nvox) return;
+  double R[9], M[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  const int g = grain[v];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) R[k] = __ldg(grainR + 9 * g + k);
+#pragma unroll
+  for (int a = 0; a < 12; ++a) {
+    const double d = dgam[a * nvox + v];
+    const double gs = d * 0.40824829046386301637;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) M[3 * i + j] = fma(gs, (double)(FCC_S[a][i] * FCC_M[a][j]), M[3 * i + j]);
+    const double ad = fabs(d);
+    const double r0 = rho[a * nvox + v];
+    rho[a * nvox + v] = (r0 + ad / (b * ell[a * nvox + v])) / (1.0 + 2.0 * yc * ad / b);
+  }
+  double T[9], Ms[9], Fpo[9], Fpn[9];
+  mat3_mult(M, R, T);
+  mat3_mul(R, T, Ms);      // R M R^T
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Fpo[k] = Fp[k * nvox + v];
+  mat3_mul(Ms, Fpo, Fpn);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Fp[k * nvox + v] = Fpn[k];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) Sc[k * nvox + v] = S[k * nvox + v];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const double f = F[k * nvox + v];
+    dFl[k * nvox + v] = f - Fc[k * nvox + v];
+    Fc[k * nvox + v] = f;
+    Pc[k * nvox + v] = P[k * nvox + v];
+  }
+}
+
+__device__ __forceinline__ void cauchy(const double* P, const double* F, double* sig) {
+  double T[9];
+  mat3_mult(P, F, T);      // P F^T
+  const double J = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+                   F[2] * (F[3] * F[7] - F[4] * F[6]);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) sig[k] = T[k] / J;
+}
+
+// partial sums of P, sigma, F (27 values) over the committed state
+__global__ void __launch_bounds__(RVE_RED_THREADS) k_macro(size_t nvox, const double* __restrict__ P,
+                                                           const double* __restrict__ F, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  double acc[27];
+#pragma unroll
+  for (int c = 0; c < 27; ++c) acc[c] = 0.0;
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (size_t)gridDim.x * blockDim.x) {
+    double Pv[9], Fv[9], sg[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) { Pv[k] = P[k * nvox + v]; Fv[k] = F[k * nvox + v]; }
+    cauchy(Pv, Fv, sg);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) { acc[k] += Pv[k]; acc[9 + k] += sg[k]; acc[18 + k] += Fv[k]; }
+  }
+  for (int c = 0; c < 27; ++c) {
+    const double s = block_sum(acc[c], sh);
+    if (threadIdx.x == 0) partial[(size_t)c * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// derived output fields: 0 = Cauchy stress (9), 1 = von Mises (1), 2 = S in the sample frame (6)
+__global__ void k_output(size_t nvox, int which, const int32_t* __restrict__ grain, const double* __restrict__ grainR,
+                         const double* __restrict__ P, const double* __restrict__ F, const double* __restrict__ Sc,
+                         double* __restrict__ out) {
+  const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nvox) return;
+  if (which == 2) {
+    double R[9], Sf[9], T[9], Ss[9];
+    const int g = grain[v];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) R[k] = __ldg(grainR + 9 * g + k);
+    double s6[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s6[k] = Sc[k * nvox + v];
+    Sf[0] = s6[0]; Sf[4] = s6[1]; Sf[8] = s6[2];
+    Sf[5] = Sf[7] = s6[3]; Sf[2] = Sf[6] = s6[4]; Sf[1] = Sf[3] = s6[5];
+    mat3_mult(Sf, R, T);
+    mat3_mul(R, T, Ss);    // R S R^T
+    const int vi[6] = {0, 4, 8, 5, 2, 1};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) out[k * nvox + v] = Ss[vi[k]];
+    return;
+  }
+  double Pv[9], Fv[9], sg[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) { Pv[k] = P[k * nvox + v]; Fv[k] = F[k * nvox + v]; }
+  cauchy(Pv, Fv, sg);
+  if (which == 0) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) out[k * nvox + v] = sg[k];
+  } else {
+    const double m = (sg[0] + sg[4] + sg[8]) / 3.0;
+    double s2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const double d = 0.5 * (sg[3 * i + j] + sg[3 * j + i]) - (i == j ? m : 0.0);
+        s2 += d * d;
+      }
+    out[v] = sqrt(1.5 * s2);
+  }
+}
+
+unsigned grid_for(size_t n, int threads) {
+  size_t b = (n + threads - 1) / threads;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_tangent_apply(const rve_s* h, int first, cudaStream_t s) {
+  k_tangent_apply<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, h->K[h->cur], h->r, h->p, h->t, h->dscal,
+                                                             first, h->partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_reduce_final(h, RED_PKP_ALPHA, s);
+}
+
+cudaError_t launch_cg_update(const rve_s* h, cudaStream_t s) {
+  k_cg_update<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(9 * h->nvox, h->x, h->r, h->p, h->q, h->dscal, h->partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_reduce_final(h, RED_RR_BETA, s);
+}
+
+cudaError_t launch_cg_init(const rve_s* h, cudaStream_t s) {
+  k_cg_init<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(9 * h->nvox, h->x, h->r, h->R, h->partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_reduce_final(h, RED_RR_INIT, s);
+}
+
+cudaError_t launch_norm2(const rve_s* h, const double* a, int ncomp, cudaStream_t s) {
+  k_norm2<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>((size_t)ncomp * h->nvox, a, h->partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_reduce_final(h, RED_NORM, s);
+}
+
+cudaError_t launch_reduce_final(const rve_s* h, int mode, cudaStream_t s) {
+  const int nval = mode == RED_MACRO ? 27 : 1;
+  k_reduce_final<<<1, 1024, 0, s>>>(h->partial, RVE_RED_BLOCKS, nval, mode, h->dscal);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_F(const rve_s* h, double lambda, cudaStream_t s) {
+  k_axpy<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(9 * h->nvox, h->F, h->x, lambda);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_predictor(const rve_s* h, const double* dFb, const double* dFb_prev, double ratio,
+                             int extrapolate, cudaStream_t s) {
+  Nine sh;
+  for (int k = 0; k < 9; ++k) sh.v[k] = dFb[k] - (extrapolate ? ratio * dFb_prev[k] : 0.0);
+  k_predictor<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, h->F, h->F_c, h->dF_last, sh, ratio, extrapolate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_commit(const rve_s* h, cudaStream_t s) {
+  k_commit<<<grid_for(h->nvox, 128), 128, 0, s>>>(h->nvox, h->grain, h->grainR, h->dgam[h->cur], h->S[h->cur],
+                                                  h->ell, h->F, h->F_c, h->dF_last, h->Fp, h->S_c, h->rho_ssd,
+                                                  h->P[h->cur], h->P_c, h->mat.b, h->mat.yc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_macro(const rve_s* h, cudaStream_t s) {
+  k_macro<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, h->P_c, h->F_c, h->partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_reduce_final(h, RED_MACRO, s);
+}
+
+cudaError_t launch_output_field(const rve_s* h, int which, const double* P, const double* S, double* dst,
+                               cudaStream_t s) {
+  k_output<<<grid_for(h->nvox, 128), 128, 0, s>>>(h->nvox, which, h->grain, h->grainR, P, h->F_c, S, dst);
+  return cudaGetLastError();
+}
