@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 FFT-Galerkin strain-gradient crystal-plasticity
+increment: the 64^3-voxel, 100-grain Cu polycrystal in uniaxial tension to 5 %
+in 50 increments (strain rate 1e-3 /s), FP64 throughout.
+
+One step = one strain increment (Nye curl and hardening, Newton-CG
+equilibrium with the local update and tangent, commit).  Metric:
+voxel-iterations/s = voxels x conjugate-gradient mat-vecs / time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank runs an independent
+replica (the increment does not shard); value = all ranks' voxel-iterations /
+max-over-ranks time.  --impl reference times the FP64 CPU oracle on the same
+workload (a bounded sample per step, see oracle_sample()).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import rvegen  # noqa: E402
+
+WORKLOAD = "cu64"
+FP64_PEAK_GFLOPS = 152 * 4 * 2.070   # 152 SMs x 2 DFMA (4 flop) per clock x 2.07 GHz = 1258.6
+# per-increment counts of the GPU path on this workload (local evaluations,
+# CG iterations), used to compose the CPU oracle's time per increment
+REF_EVALS_PER_INC = 6.0
+REF_CG_PER_INC = 500.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=47)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(rvegen.WORKLOADS))
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------- roofline
+def kernel_models(n0, n1, n2):
+    """Algorithmic FP64 flops and bytes per launch of each kernel category
+    (FFTs: 2.5 N log2 N per real and 5 N log2 N per complex transform)."""
+    nvox = n0 * n1 * n2
+    nkx = n0 // 2 + 1
+    nspec = nkx * n1 * n2
+    lg = math.log2
+    fx = 9 * n2 * n1 * 2.5 * n0 * lg(n0)
+    fy = 9 * n2 * nkx * 5.0 * n1 * lg(n1)
+    fz = 9 * nkx * n1 * 2 * 5.0 * n2 * lg(n2) + 9 * nspec * 6.0
+    return {
+        "fft_x_r2c": (fx, 9 * nvox * 8 + 9 * nspec * 16),
+        "fft_y": (fy, 2 * 9 * nspec * 16),
+        "fft_z_op": (fz, 2 * 9 * nspec * 16),
+        "fft_x_c2r": (fx, 9 * nvox * 8 + 9 * nspec * 16),
+        "tangent_apply": (nvox * (162 + 18 + 18), nvox * (81 + 9 + 9 + 9 + 9) * 8),
+        "cg_update": (9 * nvox * 6, 9 * nvox * 5 * 8),
+    }
+
+
+def roofline(stats, shape, peaks):
+    models = kernel_models(*shape)
+    timed = {k: v for k, v in stats.items() if v[0] > 0 and v[1] > 0}
+    if not timed:
+        return None, None
+    dom = max(timed, key=lambda k: timed[k][1])
+    n, ms = timed[dom]
+    avg_s = ms / n / 1e3
+    out = {"kernel": dom, "launches": n, "avg_us": avg_s * 1e6, "share": ms / sum(v[1] for v in timed.values())}
+    if dom in models:
+        flops, nbytes = models[dom]
+        t_alu = flops / (FP64_PEAK_GFLOPS * 1e9)
+        t_hbm = nbytes / (peaks["hbm_gbs"] * 1e9)
+        if t_alu >= t_hbm:
+            ach = flops / avg_s / 1e9
+            out.update(bound="alu", achieved=ach, peak=FP64_PEAK_GFLOPS, unit="GFLOP/s (FP64)", frac=ach / FP64_PEAK_GFLOPS)
+        else:
+            ach = nbytes / avg_s / 1e9
+            out.update(bound="hbm", achieved=ach, peak=peaks["hbm_gbs"], unit="GB/s", frac=ach / peaks["hbm_gbs"])
+        out["algorithmic_flops"] = flops
+        out["algorithmic_bytes"] = nbytes
+    return dom, out
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_sample(wl, frac=0.08, n_cg=2, seed=0):
+    """Bounded sample of the FP64 CPU oracle on the workload: the local update
+    with tangent on a seeded subset of grains holding about `frac` of the
+    voxels, and n_cg conjugate-gradient iterations on the full grid.  Returns
+    the composed seconds per increment for REF_EVALS_PER_INC local
+    evaluations and REF_CG_PER_INC CG iterations, and the sample's own CPU
+    seconds."""
+    from oracle import solver
+    from oracle import spectral as sp
+    gid, quat, mat = wl.inputs()
+    o = solver.RVE(gid, quat, mat, wl.edge)
+    nv = gid.size
+    t0 = time.perf_counter()
+    tauc, ell = o.hardening()
+    t_hard = time.perf_counter() - t0
+    F = o.F + (wl.dFbar() * rvegen.UNIAXIAL_X_MASK).reshape(3, 3)
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(len(o.grains))
+    chosen, count = [], 0
+    for gi in order:
+        chosen.append(o.grains[gi])
+        count += len(o.grains[gi]["idx"])
+        if count >= frac * nv:
+            break
+    keep = o.grains
+    o.grains = chosen
+    idx = np.concatenate([g["idx"] for g in chosen])
+    t0 = time.perf_counter()
+    P, K, S, M, dg, lit, lf = o.constitutive(F, tauc, o.S, wl.dt)
+    t_eval = (time.perf_counter() - t0) / len(idx)
+    o.grains = keep
+    Kfull = np.resize(K[idx], (nv, 3, 3, 3, 3))
+    R = o.flat(sp.project(o.field(np.resize(P[idx], (nv, 3, 3))), rvegen.UNIAXIAL_X_MASK, o.h))
+    o.opts.max_cg = n_cg
+    o.opts.cg_tol = 1e-300
+    t0 = time.perf_counter()
+    o.cg(Kfull, -R, rvegen.UNIAXIAL_X_MASK)
+    t_cg = (time.perf_counter() - t0) / n_cg
+    per_inc = REF_EVALS_PER_INC * nv * t_eval + REF_CG_PER_INC * t_cg + t_hard
+    sample_s = t_hard + t_eval * len(idx) + t_cg * n_cg
+    return per_inc, sample_s, len(idx), t_eval, t_cg
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------- main
+def main():
+    a = parse()
+    wl = rvegen.WORKLOADS[a.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    nvox = wl.n ** 3
+    config = {"workload": f"{wl.name}: {wl.n}^3 voxels, {wl.n_grains} seeded Voronoi grains, {wl.material}, "
+                          f"uniaxial tension {wl.strain:.0%} in {wl.increments} increments at {wl.rate:g}/s",
+              "voxels": nvox, "grains": wl.n_grains, "dt_s": wl.dt,
+              "l2": "inputs larger than L2 (working set ~1 GB: tangent fields 2 x 170 MB)",
+              "parallelism": f"replicas x{a.gpus}"}
+
+    if a.impl == "reference":
+        if world > 1 and rank != 0:
+            return
+        times = []
+        samp = None
+        for k in range(a.warmup + a.steps):
+            per_inc, sample_s, nsub, t_eval, t_cg = oracle_sample(wl, frac=0.02, n_cg=1, seed=k)
+            if k >= a.warmup:
+                times.append(per_inc)
+                samp = (sample_s, nsub)
+        ms = 1e3 * statistics.mean(times)
+        value = nvox * REF_CG_PER_INC / (ms / 1e3)
+        line = {"impl": "reference", "metric": "voxel-iterations/s", "value": value, "unit": "voxel-iter/s",
+                "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": value, "unit": "voxel-iter/s", "cores": cpu_cores(), "kind": "oracle",
+                                 "sample": f"per step: oracle local update + tangent on {samp[1]} voxels and 1 CG "
+                                           f"iteration on the full grid ({samp[0]:.1f} s), composed to "
+                                           f"{REF_EVALS_PER_INC:g} evaluations + {REF_CG_PER_INC:g} CG iterations "
+                                           "per increment"},
+                "e2e": {"value": value, "unit": "voxel-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    import paper_1910_01946_gb300 as pkg
+    from paper_1910_01946_gb300 import _build
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    pkg.load_library()
+    peaks = load_peaks()
+    gid, quat, mat = wl.inputs()
+    mask = rvegen.UNIAXIAL_X_MASK
+    Pbar = np.zeros(9)
+    dev = torch.device("cuda", local_rank)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+
+    # ---- device-resident run (inputs already on the GPU)
+    rve = pkg.RVE(gid, quat, mat, wl.edge, device=dev)
+    stream = rve.stream
+    for _ in range(a.warmup):
+        rve.step(wl.dFbar(), mask, Pbar, wl.dt)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    smi_index = vis.split(",")[local_rank] if vis else str(local_rank)
+    clocks = ClockSampler(smi_index)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    rve.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    cg_total, newton_total, evals = 0, 0, 0
+    for _ in range(a.steps):
+        info = rve.step(wl.dFbar(), mask, Pbar, wl.dt)
+        cg_total += info["cg_iters_total"]
+        newton_total += info["newton_iters"]
+    ev1.record(stream)
+    barrier()
+    clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    stats = rve.kernel_stats()
+    rve.profile(False)
+    evals = stats["constitutive"][0]
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    cg_t = torch.tensor([cg_total], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(cg_t, op=dist.ReduceOp.SUM)
+    ms_max = float(ms_t.item())
+    value = nvox * float(cg_t.item()) / (ms_max / 1e3)
+    P_macro, sig_macro = rve.macro_stress()
+    launches = int(sum(v[0] for v in stats.values()))
+    rve.close()
+    del rve
+    torch.cuda.empty_cache()
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not a.no_e2e:
+        sig_h = torch.empty((9, nvox), dtype=torch.float64).pin_memory()
+        gnd_h = torch.empty((12, nvox), dtype=torch.float64).pin_memory()
+        load_h = torch.empty(9 + 9, dtype=torch.float64).pin_memory().numpy()
+        r2 = pkg.RVE(gid, quat, mat, wl.edge, device=dev)
+        cg2 = 0
+        h2d = 9 * 8 + 9 + 9 * 8
+        d2h = sig_h.numel() * 8 + gnd_h.numel() * 8 + 2 * 9 * 8
+
+        def e2e_step():
+            load_h[:9] = wl.dFbar()
+            load_h[9:] = Pbar
+            info = r2.step(load_h[:9], mask, load_h[9:], wl.dt)
+            pkg.rve_get_fields(r2.h, pkg.FIELDS["SIGMA"][0], sig_h.data_ptr(), sig_h.numel() * 8, 0)
+            pkg.rve_get_fields(r2.h, pkg.FIELDS["RHO_GND"][0], gnd_h.data_ptr(), gnd_h.numel() * 8, 0)
+            r2.macro_stress()
+            return info
+
+        for _ in range(a.warmup):
+            e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            cg2 += e2e_step()["cg_iters_total"]
+        barrier()
+        el = time.perf_counter() - t0
+        el_t = torch.tensor([el], dtype=torch.float64, device=dev)
+        cg2_t = torch.tensor([cg2], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(el_t, op=dist.ReduceOp.MAX)
+            dist.all_reduce(cg2_t, op=dist.ReduceOp.SUM)
+        e2e = {"value": nvox * float(cg2_t.item()) / float(el_t.item()), "unit": "voxel-iter/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": 1e3 * float(el_t.item()) / a.steps,
+               "path": "rve_step with host load arrays + rve_get_fields(SIGMA, RHO_GND) to pinned host + macro stress"}
+        r2.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    dom, roof = roofline(stats, (wl.n, wl.n, wl.n), peaks)
+    roof_line = None
+    if roof is not None and "bound" in roof:
+        roof_line = {"bound": roof["bound"], "achieved": roof["achieved"], "peak": roof["peak"], "unit": roof["unit"],
+                     "frac": roof["frac"], "traffic": None, "kernel": dom, "launches": roof["launches"],
+                     "avg_us": roof["avg_us"], "share_of_kernel_time": roof["share"],
+                     "peak_source": "FP64: derived 152 SM x 4 flop/clk x 2070 MHz" if roof["bound"] == "alu"
+                     else f"HBM: MEASURED_PEAKS.json ({peaks['source']})"}
+    cpu = None
+    if not a.no_cpu_baseline:
+        per_inc, sample_s, nsub, t_eval, t_cg = oracle_sample(wl)
+        evals_per_inc = evals / a.steps
+        cg_per_inc = cg_total / a.steps
+        t_inc = evals_per_inc * nvox * t_eval + cg_per_inc * t_cg
+        cpu = {"value": nvox * cg_per_inc / t_inc, "unit": "voxel-iter/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"oracle local update + tangent on {nsub} voxels ({t_eval * 1e6:.0f} us/voxel) and 2 CG "
+                         f"iterations on the full grid ({t_cg:.2f} s each), {sample_s:.1f} s in all; composed with "
+                         f"this run's {evals_per_inc:.1f} evaluations and {cg_per_inc:.0f} CG iterations per increment"}
+    line = {"metric": "voxel-iterations/s", "value": value, "unit": "voxel-iter/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+            "e2e": e2e, "gpu_launches": launches, "roofline": roof_line, "cpu_baseline": cpu,
+            "clocks": clocks.summary(),
+            "detail": {"voxel_increments_per_s": world * nvox * a.steps / (ms_max / 1e3),
+                       "cg_iters_per_increment": cg_total / a.steps,
+                       "newton_iters_per_increment": newton_total / a.steps,
+                       "local_evals_per_increment": evals / a.steps,
+                       "macro_P11_MPa": float(P_macro[0, 0]), "macro_sigma11_MPa": float(sig_macro[0, 0]),
+                       "kernels_ms": {k: round(v[1], 3) for k, v in stats.items()},
+                       "kernels_launches": {k: v[0] for k, v in stats.items()}}}
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

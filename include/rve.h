@@ -187,6 +187,21 @@ size_t rve_checkpoint_bytes(const rve_t* rve);
 rve_status rve_checkpoint(rve_t* rve, void* host_buf, size_t bytes);
 rve_status rve_restore(rve_t* rve, const void* host_buf, size_t bytes);
 
+/* Kernel accounting.  Every kernel launch is counted per category (always on).
+ * With rve_profile(rve, 1) each launch is also bracketed by CUDA events on
+ * the handle's stream and its device time accumulated per category (the
+ * events are resolved at the library's own host synchronisation points);
+ * rve_profile(rve, 0) stops timing.  Both calls reset the counters.
+ * rve_kernel_stats copies RVE_K_COUNT launch counts and milliseconds (host
+ * arrays, either may be NULL). */
+enum {
+  RVE_K_FFT_X_R2C = 0, RVE_K_FFT_Y = 1, RVE_K_FFT_Z_OP = 2, RVE_K_FFT_X_C2R = 3,
+  RVE_K_CONSTITUTIVE = 4, RVE_K_HARDENING = 5, RVE_K_TANGENT_APPLY = 6, RVE_K_CG_UPDATE = 7,
+  RVE_K_REDUCE = 8, RVE_K_OTHER = 9, RVE_K_COUNT = 10
+};
+rve_status rve_profile(rve_t* rve, int enable);
+rve_status rve_kernel_stats(rve_t* rve, int64_t* launches, double* ms);
+
 const char* rve_last_error(const rve_t* rve);
 void rve_destroy(rve_t* rve);
 

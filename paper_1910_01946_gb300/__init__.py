@@ -29,6 +29,8 @@ FIELDS = {"F": (0, 9), "P": (1, 9), "FP": (2, 9), "S": (3, 6), "SIGMA": (4, 9), 
           "DGAM": (11, 12), "TANGENT": (12, 81), "GRAIN": (13, 1), "P_EVAL": (14, 9), "S_EVAL": (15, 6)}
 
 MAX_NEWTON_LOG = 64
+KERNELS = ("fft_x_r2c", "fft_y", "fft_z_op", "fft_x_c2r", "constitutive", "hardening", "tangent_apply",
+           "cg_update", "reduce", "other")
 
 
 class rve_material(C.Structure):
@@ -68,6 +70,8 @@ _SIGS = {
     "rve_checkpoint_bytes": (C.c_size_t, [C.c_void_p]),
     "rve_checkpoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "rve_restore": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "rve_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "rve_kernel_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "rve_last_error": (C.c_char_p, [C.c_void_p]),
     "rve_destroy": (None, [C.c_void_p]),
 }
@@ -155,6 +159,14 @@ def rve_checkpoint(h, buf):
 
 def rve_restore(h, buf):
     return load_library().rve_restore(h, _ptr(buf), buf.nbytes)
+
+
+def rve_profile(h, enable):
+    return load_library().rve_profile(h, int(enable))
+
+
+def rve_kernel_stats(h, launches, ms):
+    return load_library().rve_kernel_stats(h, _ptr(launches), _ptr(ms))
 
 
 def rve_last_error(h):
@@ -289,6 +301,17 @@ class RVE:
         self._check(rve_project(self.h, np.ascontiguousarray(mask, dtype=np.uint8).reshape(9), X.data_ptr(),
                                 Y.data_ptr()), "rve_project")
         return Y
+
+    def profile(self, enable: bool):
+        """Reset the kernel counters; time every launch with CUDA events while enabled."""
+        self._check(rve_profile(self.h, enable), "rve_profile")
+
+    def kernel_stats(self):
+        """{kernel category: (launches, device milliseconds)} since the last profile() call."""
+        n = np.zeros(len(KERNELS), dtype=np.int64)
+        ms = np.zeros(len(KERNELS), dtype=np.float64)
+        self._check(rve_kernel_stats(self.h, n, ms), "rve_kernel_stats")
+        return {k: (int(n[i]), float(ms[i])) for i, k in enumerate(KERNELS)}
 
     def checkpoint(self) -> np.ndarray:
         buf = np.empty(rve_checkpoint_bytes(self.h), dtype=np.uint8)

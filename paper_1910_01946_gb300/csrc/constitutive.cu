@@ -428,8 +428,11 @@ __global__ void __launch_bounds__(128) k_constitutive(
 
 cudaError_t launch_hardening(const rve_s* h, cudaStream_t s) {
   const unsigned blocks = (unsigned)((h->nvox + 127) / 128);
-  k_hardening<<<blocks, 128, 0, s>>>(h->nvox, h->grain, h->grainR, h->qhat, h->Apinv, h->screw_of, h->nye,
+  {
+    ProfScope ps_(h, RVE_K_HARDENING, s);
+    k_hardening<<<blocks, 128, 0, s>>>(h->nvox, h->grain, h->grainR, h->qhat, h->Apinv, h->screw_of, h->nye,
                                      h->rho_ssd, h->Fp, h->rho18, h->rho_gnd, h->tauc, h->ell, h->Fp0inv, h->cst);
+  }
   return cudaGetLastError();
 }
 
@@ -437,8 +440,11 @@ cudaError_t launch_constitutive(const rve_s* h, double dt, double lambda, int ou
                                 cudaStream_t s) {
   const unsigned blocks = (unsigned)((h->nvox + 127) / 128);
   const double* warm = warm_buf < 0 ? h->S_c : h->S[warm_buf];
-  k_constitutive<<<blocks, 128, 0, s>>>(h->nvox, h->grain, h->grainR, h->F, h->x, lambda, h->Fp0inv, h->tauc,
+  {
+    ProfScope ps_(h, RVE_K_CONSTITUTIVE, s);
+    k_constitutive<<<blocks, 128, 0, s>>>(h->nvox, h->grain, h->grainR, h->F, h->x, lambda, h->Fp0inv, h->tauc,
                                         warm, h->P[out_buf], h->K[out_buf], h->S[out_buf], h->dgam[out_buf],
                                         h->dcount, dt, h->cst);
+  }
   return cudaGetLastError();
 }

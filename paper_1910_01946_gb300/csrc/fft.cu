@@ -318,11 +318,17 @@ cudaError_t launch_fft_forward(const rve_s* h, const double* in, cudaStream_t s)
   const int rpb = rows_per_block(h->n0, h->n1);
   dim3 gx(h->n1 / 2 / rpb, h->n2, 9);
   size_t shx = 2 * (size_t)rpb * h->n0 * sizeof(cplx);
-  k_fft_x_r2c<<<gx, 256, shx, s>>>(in, h->spec, h->n0, h->n1, h->n2, h->nkx, rpb, to_dev(h->plan[0]), h->ax[0].tw);
+  {
+    ProfScope ps_(h, RVE_K_FFT_X_R2C, s);
+    k_fft_x_r2c<<<gx, 256, shx, s>>>(in, h->spec, h->n0, h->n1, h->n2, h->nkx, rpb, to_dev(h->plan[0]), h->ax[0].tw);
+  }
   const int ty = tile_y(h->n1);
   dim3 gy((h->nkx + ty - 1) / ty, h->n2, 9);
   size_t shy = 2 * (size_t)ty * h->n1 * sizeof(cplx);
-  k_fft_y<<<gy, 256, shy, s>>>(h->spec, h->n1, h->n2, h->nkx, ty, to_dev(h->plan[1]), h->ax[1].tw, -1);
+  {
+    ProfScope ps_(h, RVE_K_FFT_Y, s);
+    k_fft_y<<<gy, 256, shy, s>>>(h->spec, h->n1, h->n2, h->nkx, ty, to_dev(h->plan[1]), h->ax[1].tw, -1);
+  }
   return cudaGetLastError();
 }
 
@@ -334,7 +340,10 @@ cudaError_t launch_fft_op(const rve_s* h, const SpecParams& sp, cudaStream_t s) 
   T.tan0 = h->ax[0].tanh_; T.tan1 = h->ax[1].tanh_; T.tan2 = h->ax[2].tanh_;
   T.nyq0 = h->ax[0].nyq; T.nyq1 = h->ax[1].nyq; T.nyq2 = h->ax[2].nyq;
   T.ph0 = h->ax[0].ph; T.ph1 = h->ax[1].ph; T.ph2 = h->ax[2].ph;
-  k_fft_z_op<<<g, 256, sh, s>>>(h->spec, h->n1, h->n2, h->nkx, tz, to_dev(h->plan[2]), h->ax[2].tw, T, sp);
+  {
+    ProfScope ps_(h, RVE_K_FFT_Z_OP, s);
+    k_fft_z_op<<<g, 256, sh, s>>>(h->spec, h->n1, h->n2, h->nkx, tz, to_dev(h->plan[2]), h->ax[2].tw, T, sp);
+  }
   return cudaGetLastError();
 }
 
@@ -342,10 +351,16 @@ cudaError_t launch_fft_inverse(const rve_s* h, double* out, cudaStream_t s) {
   const int ty = tile_y(h->n1);
   dim3 gy((h->nkx + ty - 1) / ty, h->n2, 9);
   size_t shy = 2 * (size_t)ty * h->n1 * sizeof(cplx);
-  k_fft_y<<<gy, 256, shy, s>>>(h->spec, h->n1, h->n2, h->nkx, ty, to_dev(h->plan[1]), h->ax[1].tw, +1);
+  {
+    ProfScope ps_(h, RVE_K_FFT_Y, s);
+    k_fft_y<<<gy, 256, shy, s>>>(h->spec, h->n1, h->n2, h->nkx, ty, to_dev(h->plan[1]), h->ax[1].tw, +1);
+  }
   const int rpb = rows_per_block(h->n0, h->n1);
   dim3 gx(h->n1 / 2 / rpb, h->n2, 9);
   size_t shx = 2 * (size_t)rpb * h->n0 * sizeof(cplx);
-  k_fft_x_c2r<<<gx, 256, shx, s>>>(h->spec, out, h->n0, h->n1, h->n2, h->nkx, rpb, to_dev(h->plan[0]), h->ax[0].tw);
+  {
+    ProfScope ps_(h, RVE_K_FFT_X_C2R, s);
+    k_fft_x_c2r<<<gx, 256, shx, s>>>(h->spec, out, h->n0, h->n1, h->n2, h->nkx, rpb, to_dev(h->plan[0]), h->ax[0].tw);
+  }
   return cudaGetLastError();
 }

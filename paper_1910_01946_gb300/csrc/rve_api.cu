@@ -209,12 +209,14 @@ rve_status read_scalars(rve_s* h) {
   RVE_CUDA(h, cudaMemcpyAsync(h->hscal, h->dscal, 64 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   RVE_CUDA(h, cudaMemcpyAsync(h->hcount, h->dcount, 16 * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
   RVE_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (h->prof.on) h->prof.resolve();
   return RVE_OK;
 }
 
 rve_status read_rr(rve_s* h, double* rr) {
   RVE_CUDA(h, cudaMemcpyAsync(h->hscal + DS_RR, h->dscal + DS_RR, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   RVE_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (h->prof.on) h->prof.resolve();
   *rr = h->hscal[DS_RR];
   return RVE_OK;
 }
@@ -307,6 +309,53 @@ int ncomp_of(uint32_t which) {
 }
 
 }  // namespace
+
+cudaEvent_t Prof::take() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void Prof::begin(int cat, cudaStream_t s, cudaEvent_t* a) {
+  ++launches[cat];
+  if (!on) return;
+  *a = take();
+  if (*a) cudaEventRecord(*a, s);
+}
+
+void Prof::end(int cat, cudaStream_t s, cudaEvent_t a) {
+  if (!on || !a) return;
+  cudaEvent_t b = take();
+  if (!b) { pool.push_back(a); return; }
+  cudaEventRecord(b, s);
+  pending.push_back({cat, a, b});
+}
+
+void Prof::resolve() {
+  for (auto& p : pending) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) ms[p.cat] += t;
+    pool.push_back(p.a);
+    pool.push_back(p.b);
+  }
+  pending.clear();
+}
+
+void Prof::reset() {
+  resolve();
+  for (int k = 0; k < RVE_K_COUNT; ++k) { launches[k] = 0; ms[k] = 0.0; }
+}
+
+void Prof::destroy() {
+  resolve();
+  for (auto e : pool) cudaEventDestroy(e);
+  pool.clear();
+}
 
 extern "C" {
 
@@ -706,11 +755,31 @@ rve_status rve_restore(rve_t* h, const void* host_buf, size_t bytes) {
   return RVE_OK;
 }
 
+rve_status rve_profile(rve_t* h, int enable) {
+  if (!h) return RVE_EINVAL;
+  RVE_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->prof.reset();
+  h->prof.on = enable != 0;
+  return RVE_OK;
+}
+
+rve_status rve_kernel_stats(rve_t* h, int64_t* launches, double* ms) {
+  if (!h) return RVE_EINVAL;
+  RVE_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->prof.resolve();
+  for (int k = 0; k < RVE_K_COUNT; ++k) {
+    if (launches) launches[k] = h->prof.launches[k];
+    if (ms) ms[k] = h->prof.ms[k];
+  }
+  return RVE_OK;
+}
+
 const char* rve_last_error(const rve_t* h) { return h ? h->err.c_str() : "null handle"; }
 
 void rve_destroy(rve_t* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  h->prof.destroy();
   cudaFreeHost(h->hscal);
   cudaFreeHost(h->hcount);
   delete h;

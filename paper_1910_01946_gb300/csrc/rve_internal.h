@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <vector>
 
 #include "../../include/rve.h"
 
@@ -46,6 +47,22 @@ struct Consts {        // material constants read by the hardening and constitut
   int max_local, max_halvings;
 };
 
+// Launch accounting: every kernel launch goes through prof_begin/prof_end.
+struct Prof {
+  bool on = false;
+  int64_t launches[RVE_K_COUNT] = {0};
+  double ms[RVE_K_COUNT] = {0};
+  struct Pending { int cat; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t take();
+  void begin(int cat, cudaStream_t s, cudaEvent_t* a);
+  void end(int cat, cudaStream_t s, cudaEvent_t a);
+  void resolve();      // after a host synchronisation
+  void reset();
+  void destroy();
+};
+
 struct rve_s {
   int n0, n1, n2, nkx;
   size_t nvox, nspec;   // nspec = nkx * n1 * n2
@@ -83,6 +100,14 @@ struct rve_s {
   double dt_prev;
   int increment;
   std::string err;
+  mutable Prof prof;
+};
+
+// bracket one kernel launch of category `cat` on stream `s`
+struct ProfScope {
+  Prof& p; int cat; cudaStream_t s; cudaEvent_t a = nullptr;
+  ProfScope(const rve_s* h, int c, cudaStream_t st) : p(h->prof), cat(c), s(st) { p.begin(cat, s, &a); }
+  ~ProfScope() { p.end(cat, s, a); }
 };
 
 // device scalar slots

@@ -266,29 +266,41 @@ unsigned grid_for(size_t n, int threads) {
 }  // namespace
 
 cudaError_t launch_tangent_apply(const rve_s* h, int first, cudaStream_t s) {
-  k_tangent_apply<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, h->K[h->cur], h->r, h->p, h->t, h->dscal,
+  {
+    ProfScope ps_(h, RVE_K_TANGENT_APPLY, s);
+    k_tangent_apply<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, h->K[h->cur], h->r, h->p, h->t, h->dscal,
                                                              first, h->partial);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_reduce_final(h, RED_PKP_ALPHA, s);
 }
 
 cudaError_t launch_cg_update(const rve_s* h, cudaStream_t s) {
-  k_cg_update<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(9 * h->nvox, h->x, h->r, h->p, h->q, h->dscal, h->partial);
+  {
+    ProfScope ps_(h, RVE_K_CG_UPDATE, s);
+    k_cg_update<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(9 * h->nvox, h->x, h->r, h->p, h->q, h->dscal, h->partial);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_reduce_final(h, RED_RR_BETA, s);
 }
 
 cudaError_t launch_cg_init(const rve_s* h, cudaStream_t s) {
-  k_cg_init<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(9 * h->nvox, h->x, h->r, h->R, h->partial);
+  {
+    ProfScope ps_(h, RVE_K_OTHER, s);
+    k_cg_init<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(9 * h->nvox, h->x, h->r, h->R, h->partial);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_reduce_final(h, RED_RR_INIT, s);
 }
 
 cudaError_t launch_norm2(const rve_s* h, const double* a, int ncomp, cudaStream_t s) {
-  k_norm2<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>((size_t)ncomp * h->nvox, a, h->partial);
+  {
+    ProfScope ps_(h, RVE_K_REDUCE, s);
+    k_norm2<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>((size_t)ncomp * h->nvox, a, h->partial);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_reduce_final(h, RED_NORM, s);
@@ -296,12 +308,18 @@ cudaError_t launch_norm2(const rve_s* h, const double* a, int ncomp, cudaStream_
 
 cudaError_t launch_reduce_final(const rve_s* h, int mode, cudaStream_t s) {
   const int nval = mode == RED_MACRO ? 27 : 1;
-  k_reduce_final<<<1, 1024, 0, s>>>(h->partial, RVE_RED_BLOCKS, nval, mode, h->dscal);
+  {
+    ProfScope ps_(h, RVE_K_REDUCE, s);
+    k_reduce_final<<<1, 1024, 0, s>>>(h->partial, RVE_RED_BLOCKS, nval, mode, h->dscal);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_axpy_F(const rve_s* h, double lambda, cudaStream_t s) {
-  k_axpy<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(9 * h->nvox, h->F, h->x, lambda);
+  {
+    ProfScope ps_(h, RVE_K_OTHER, s);
+    k_axpy<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(9 * h->nvox, h->F, h->x, lambda);
+  }
   return cudaGetLastError();
 }
 
@@ -309,19 +327,28 @@ cudaError_t launch_predictor(const rve_s* h, const double* dFb, const double* dF
                              int extrapolate, cudaStream_t s) {
   Nine sh;
   for (int k = 0; k < 9; ++k) sh.v[k] = dFb[k] - (extrapolate ? ratio * dFb_prev[k] : 0.0);
-  k_predictor<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, h->F, h->F_c, h->dF_last, sh, ratio, extrapolate);
+  {
+    ProfScope ps_(h, RVE_K_OTHER, s);
+    k_predictor<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, h->F, h->F_c, h->dF_last, sh, ratio, extrapolate);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_commit(const rve_s* h, cudaStream_t s) {
-  k_commit<<<grid_for(h->nvox, 128), 128, 0, s>>>(h->nvox, h->grain, h->grainR, h->dgam[h->cur], h->S[h->cur],
+  {
+    ProfScope ps_(h, RVE_K_OTHER, s);
+    k_commit<<<grid_for(h->nvox, 128), 128, 0, s>>>(h->nvox, h->grain, h->grainR, h->dgam[h->cur], h->S[h->cur],
                                                   h->ell, h->F, h->F_c, h->dF_last, h->Fp, h->S_c, h->rho_ssd,
                                                   h->P[h->cur], h->P_c, h->mat.b, h->mat.yc);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_macro(const rve_s* h, cudaStream_t s) {
-  k_macro<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, h->P_c, h->F_c, h->partial);
+  {
+    ProfScope ps_(h, RVE_K_REDUCE, s);
+    k_macro<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, h->P_c, h->F_c, h->partial);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_reduce_final(h, RED_MACRO, s);
@@ -329,6 +356,9 @@ cudaError_t launch_macro(const rve_s* h, cudaStream_t s) {
 
 cudaError_t launch_output_field(const rve_s* h, int which, const double* P, const double* S, double* dst,
                                cudaStream_t s) {
-  k_output<<<grid_for(h->nvox, 128), 128, 0, s>>>(h->nvox, which, h->grain, h->grainR, P, h->F_c, S, dst);
+  {
+    ProfScope ps_(h, RVE_K_OTHER, s);
+    k_output<<<grid_for(h->nvox, 128), 128, 0, s>>>(h->nvox, which, h->grain, h->grainR, P, h->F_c, S, dst);
+  }
   return cudaGetLastError();
 }
