@@ -202,6 +202,37 @@ enum {
 rve_status rve_profile(rve_t* rve, int enable);
 rve_status rve_kernel_stats(rve_t* rve, int64_t* launches, double* ms);
 
+/* Allocation-free Galerkin projection (no counterpart in the paper; an
+ * addition for callers that cannot allocate device memory).
+ *
+ * Y = G*(X) exactly as rve_project computes it, for device fields X and Y
+ * (9 * n0*n1*n2 doubles each, layout as above, may alias) on an n0 x n1 x n2
+ * grid of edge L along x, under strain_mask (host, 9 bytes).  It needs no
+ * handle and no workspace: the FFT spectrum and frequency tables live in one
+ * static device array of RVE_NOALLOC_SPEC_BYTES plus about 64 KiB, which every
+ * GPU that loads the library holds until the process exits.  Meant for code
+ * that must not call cudaMalloc: for example a plug-in running under a host
+ * application whose memory manager has already reserved the device memory, or
+ * a time-critical loop that cannot afford cudaMalloc/cudaFree's implicit
+ * device-wide synchronisation.  This entry point calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *
+ * Work is queued on cuda_stream (a cudaStream_t, NULL = legacy default
+ * stream) and the call returns without waiting: synchronise the stream before
+ * reading Y.  The first call on a device looks up the device address of the
+ * static array (cudaGetSymbolAddress, once per device, with that device
+ * current); make that first call before any stream capture.  All calls share
+ * the one array, which keeps the last call's contents: calls that overlap on
+ * the GPU (different streams, or different host threads) race on it.
+ *
+ * Errors: RVE_EINVAL for bad pointers, L <= 0 or unsupported sizes (as in
+ * rve_workspace_bytes); RVE_ENOMEM when 9 * (n0/2 + 1) * n1 * n2 * 16 bytes of
+ * spectrum exceed RVE_NOALLOC_SPEC_BYTES (64^3 fits; 96^3 does not);
+ * RVE_ECUDA when a CUDA call fails. */
+#define RVE_NOALLOC_SPEC_BYTES ((size_t)32 * 1024 * 1024)
+rve_status rve_project_noalloc(int n0, int n1, int n2, double L, const uint8_t strain_mask[9],
+                               const double* d_X, double* d_Y, void* cuda_stream);
+
 const char* rve_last_error(const rve_t* rve);
 void rve_destroy(rve_t* rve);
 

@@ -72,6 +72,8 @@ _SIGS = {
     "rve_restore": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "rve_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "rve_kernel_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rve_project_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p]),
     "rve_last_error": (C.c_char_p, [C.c_void_p]),
     "rve_destroy": (None, [C.c_void_p]),
 }
@@ -167,6 +169,12 @@ def rve_profile(h, enable):
 
 def rve_kernel_stats(h, launches, ms):
     return load_library().rve_kernel_stats(h, _ptr(launches), _ptr(ms))
+
+
+def rve_project_noalloc(n0, n1, n2, L, mask, d_X, d_Y, stream):
+    """Y = G*(X) with the library's static scratch (no allocation; asynchronous on `stream`)."""
+    return load_library().rve_project_noalloc(n0, n1, n2, float(L), _ptr(mask), C.c_void_p(d_X),
+                                              C.c_void_p(d_Y), C.c_void_p(stream))
 
 
 def rve_last_error(h):
