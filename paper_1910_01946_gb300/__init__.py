@@ -30,7 +30,7 @@ FIELDS = {"F": (0, 9), "P": (1, 9), "FP": (2, 9), "S": (3, 6), "SIGMA": (4, 9), 
 
 MAX_NEWTON_LOG = 64
 KERNELS = ("fft_x_r2c", "fft_y", "fft_z_op", "fft_x_c2r", "constitutive", "hardening", "tangent_apply",
-           "cg_update", "reduce", "other")
+           "cg_update", "reduce", "other", "stencil")
 
 
 class rve_material(C.Structure):
@@ -44,7 +44,7 @@ class rve_options(C.Structure):
     _fields_ = [("L", C.c_double), ("newton_tol", C.c_double), ("cg_tol", C.c_double),
                 ("local_tol", C.c_double), ("max_newton", C.c_int32), ("max_cg", C.c_int32),
                 ("max_local", C.c_int32), ("max_halvings", C.c_int32), ("extrapolate", C.c_int32),
-                ("precision", C.c_int32)]
+                ("precision", C.c_int32), ("cg_adaptive", C.c_int32)]
 
 
 class rve_step_info(C.Structure):
@@ -187,8 +187,8 @@ def rve_destroy(h):
 
 
 # ---- handle wrapper ---------------------------------------------------------
-DEFAULT_OPTIONS = dict(newton_tol=1e-11, cg_tol=1e-11, local_tol=1e-14, max_newton=40, max_cg=2000,
-                       max_local=60, max_halvings=12, extrapolate=1, precision=0)
+DEFAULT_OPTIONS = dict(newton_tol=1e-11, cg_tol=1e-11, local_tol=1e-14, max_newton=100, max_cg=2000,
+                       max_local=60, max_halvings=12, extrapolate=1, precision=0, cg_adaptive=1)
 
 
 def make_material(m) -> rve_material:

@@ -76,3 +76,42 @@ RVE_HD double mat3_inv(const double* A, double* B) {
   B[8] = (A[0] * A[4] - A[1] * A[3]) * id;
   return det;
 }
+
+// ---- deterministic reductions shared by the reducing kernels ----
+// block-wide sum, result in thread 0 (all threads must call it)
+__device__ __forceinline__ double blk_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int w = 0; w < nw; ++w) s += sh[w];
+  }
+  __syncthreads();
+  return s;
+}
+
+// After every block has written partial[c * gridDim.x + blockIdx.x] for
+// c < nval: the block that takes the last ticket sums each value over the
+// blocks in block order (deterministic) into out[c] (thread 0) and returns
+// true; every other block returns false.
+__device__ __forceinline__ bool last_block_sums(const double* partial, int nval, unsigned int* ticket, double* sh,
+                                                double* out) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return false;
+  for (int c = 0; c < nval; ++c) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) acc += __ldcg(partial + (size_t)c * gridDim.x + i);
+    const double s = blk_sum(acc, sh);
+    if (threadIdx.x == 0) out[c] = s;
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}

@@ -34,15 +34,29 @@ PlanDev to_dev(const FFTPlan& p) {
   return d;
 }
 
-__device__ __forceinline__ cplx ld_tw(const double2* tw, int idx, int sign) {
+template <int SIGN>
+__device__ __forceinline__ cplx ld_tw(const double2* tw, int idx) {
   double2 w = __ldg(tw + idx);
-  return cmk(w.x, sign < 0 ? w.y : -w.y);
+  return cmk(w.x, SIGN < 0 ? w.y : -w.y);
 }
+
+// a * conj-or-not(w) with the sign fixed at compile time, so the negation
+// folds into the FMA operands
+template <int SIGN>
+__device__ __forceinline__ cplx twiddle(cplx a, const double2* tw, int idx) {
+  const double2 w = __ldg(tw + idx);
+  if (SIGN < 0) return cmk(fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x));
+  return cmk(fma(a.x, w.x, a.y * w.y), fma(a.y, w.x, -a.x * w.y));
+}
+
+template <int SIGN>
+__device__ __forceinline__ cplx mul_i(cplx a) { return SIGN > 0 ? cmk(-a.y, a.x) : cmk(a.y, -a.x); }
 
 // One Stockham pass of radix R over `howmany` contiguous transforms of length
 // N from src to dst (both shared memory).
+template <int SIGN>
 __device__ void stockham_pass(const cplx* __restrict__ src, cplx* __restrict__ dst, int N, int howmany,
-                              int R, int Ns, const double2* tw, int sign) {
+                              int R, int Ns, const double2* tw) {
   const int nb = N / R;
   const int total = nb * howmany;
   const int twstep = N / (Ns * R);
@@ -56,29 +70,29 @@ __device__ void stockham_pass(const cplx* __restrict__ src, cplx* __restrict__ d
     if (R == 4) {
       cplx a0 = X[j], a1 = X[j + nb], a2 = X[j + 2 * nb], a3 = X[j + 3 * nb];
       if (k) {
-        a1 = cmul(a1, ld_tw(tw, k * twstep, sign));
-        a2 = cmul(a2, ld_tw(tw, 2 * k * twstep, sign));
-        a3 = cmul(a3, ld_tw(tw, 3 * k * twstep, sign));
+        a1 = twiddle<SIGN>(a1, tw, k * twstep);
+        a2 = twiddle<SIGN>(a2, tw, 2 * k * twstep);
+        a3 = twiddle<SIGN>(a3, tw, 3 * k * twstep);
       }
-      cplx t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = cmul_i(csub(a1, a3), sign);
+      cplx t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = mul_i<SIGN>(csub(a1, a3));
       Y[d] = cadd(t0, t2);
       Y[d + Ns] = cadd(t1, t3);
       Y[d + 2 * Ns] = csub(t0, t2);
       Y[d + 3 * Ns] = csub(t1, t3);
     } else if (R == 2) {
       cplx a0 = X[j], a1 = X[j + nb];
-      if (k) a1 = cmul(a1, ld_tw(tw, k * twstep, sign));
+      if (k) a1 = twiddle<SIGN>(a1, tw, k * twstep);
       Y[d] = cadd(a0, a1);
       Y[d + Ns] = csub(a0, a1);
     } else {  // R == 3
       cplx a0 = X[j], a1 = X[j + nb], a2 = X[j + 2 * nb];
       if (k) {
-        a1 = cmul(a1, ld_tw(tw, k * twstep, sign));
-        a2 = cmul(a2, ld_tw(tw, 2 * k * twstep, sign));
+        a1 = twiddle<SIGN>(a1, tw, k * twstep);
+        a2 = twiddle<SIGN>(a2, tw, 2 * k * twstep);
       }
       const double s3 = 0.86602540378443864676;  // sqrt(3)/2
       cplx t = cadd(a1, a2);
-      cplx u = cscale(cmul_i(csub(a1, a2), sign), s3);
+      cplx u = cscale(mul_i<SIGN>(csub(a1, a2)), s3);
       cplx m = cmk(fma(-0.5, t.x, a0.x), fma(-0.5, t.y, a0.y));
       Y[d] = cadd(a0, t);
       Y[d + Ns] = cadd(m, u);
@@ -89,11 +103,12 @@ __device__ void stockham_pass(const cplx* __restrict__ src, cplx* __restrict__ d
 
 // Full transform of `howmany` contiguous length-N sequences; the caller has
 // synchronised after filling `a`.  Returns the buffer that holds the result.
-__device__ cplx* block_fft(cplx* a, cplx* b, const PlanDev& pl, int howmany, const double2* tw, int sign) {
+template <int SIGN>
+__device__ cplx* block_fft(cplx* a, cplx* b, const PlanDev& pl, int howmany, const double2* tw) {
   int Ns = 1;
   for (int p = 0; p < pl.npass; ++p) {
     const int R = pl.radix[p];
-    stockham_pass(a, b, pl.n, howmany, R, Ns, tw, sign);
+    stockham_pass<SIGN>(a, b, pl.n, howmany, R, Ns, tw);
     __syncthreads();
     cplx* t = a; a = b; b = t;
     Ns *= R;
@@ -104,7 +119,8 @@ __device__ cplx* block_fft(cplx* a, cplx* b, const PlanDev& pl, int howmany, con
 // ---------------------------------------------------------------- pass X (R2C)
 __global__ void __launch_bounds__(256) k_fft_x_r2c(const double* __restrict__ in, double2* __restrict__ spec,
                                                    int n0, int n1, int n2, int nkx, int rpb, PlanDev pl,
-                                                   const double2* __restrict__ tw) {
+                                                   const double2* __restrict__ tw, const double* __restrict__ done) {
+  if (done && *done != 0.0) return;
   extern __shared__ cplx sm[];
   cplx* a = sm;
   cplx* b = sm + rpb * n0;
@@ -117,7 +133,7 @@ __global__ void __launch_bounds__(256) k_fft_x_r2c(const double* __restrict__ in
     a[e] = cmk(src[(size_t)y0 * n0 + x], src[(size_t)(y0 + 1) * n0 + x]);
   }
   __syncthreads();
-  cplx* res = block_fft(a, b, pl, rpb, tw, -1);
+  cplx* res = block_fft<-1>(a, b, pl, rpb, tw);
   double2* dst = spec + ((size_t)f * n2 + z) * n1 * nkx;
   for (int e = threadIdx.x; e < rpb * nkx; e += blockDim.x) {
     const int jj = e / nkx, k = e - jj * nkx;
@@ -133,7 +149,8 @@ __global__ void __launch_bounds__(256) k_fft_x_r2c(const double* __restrict__ in
 // ---------------------------------------------------------------- pass X^-1 (C2R)
 __global__ void __launch_bounds__(256) k_fft_x_c2r(const double2* __restrict__ spec, double* __restrict__ out,
                                                    int n0, int n1, int n2, int nkx, int rpb, PlanDev pl,
-                                                   const double2* __restrict__ tw) {
+                                                   const double2* __restrict__ tw, const double* __restrict__ done) {
+  if (done && *done != 0.0) return;
   extern __shared__ cplx sm[];
   cplx* a = sm;
   cplx* b = sm + rpb * n0;
@@ -154,7 +171,7 @@ __global__ void __launch_bounds__(256) k_fft_x_c2r(const double2* __restrict__ s
     a[e] = cmk(A.x - B.y, A.y + B.x);  // A + i B
   }
   __syncthreads();
-  cplx* res = block_fft(a, b, pl, rpb, tw, +1);
+  cplx* res = block_fft<+1>(a, b, pl, rpb, tw);
   double* dst = out + f * nvox + (size_t)z * n1 * n0;
   for (int e = threadIdx.x; e < rpb * n0; e += blockDim.x) {
     const int jj = e / n0, x = e - jj * n0;
@@ -165,8 +182,11 @@ __global__ void __launch_bounds__(256) k_fft_x_c2r(const double2* __restrict__ s
 }
 
 // ---------------------------------------------------------------- pass Y (C2C)
+template <int SIGN>
 __global__ void __launch_bounds__(256) k_fft_y(double2* __restrict__ spec, int n1, int n2, int nkx, int tx,
-                                               PlanDev pl, const double2* __restrict__ tw, int sign) {
+                                               PlanDev pl, const double2* __restrict__ tw,
+                                               const double* __restrict__ done) {
+  if (done && *done != 0.0) return;
   extern __shared__ cplx sm[];
   cplx* a = sm;
   cplx* b = sm + tx * n1;
@@ -179,7 +199,7 @@ __global__ void __launch_bounds__(256) k_fft_y(double2* __restrict__ spec, int n
     a[t * n1 + y] = cmk(v.x, v.y);
   }
   __syncthreads();
-  cplx* res = block_fft(a, b, pl, tx, tw, sign);
+  cplx* res = block_fft<SIGN>(a, b, pl, tx, tw);
   for (int e = threadIdx.x; e < tx * n1; e += blockDim.x) {
     const int y = e / tx, t = e - y * tx;
     const int kx = kx0 + t;
@@ -191,6 +211,8 @@ __global__ void __launch_bounds__(256) k_fft_y(double2* __restrict__ spec, int n
 }
 
 struct OpTables {
+  const double* s20; const double* s21; const double* s22;
+  const double* c20; const double* c21; const double* c22;
   const double* tan0; const double* tan1; const double* tan2;
   const int8_t* nyq0; const int8_t* nyq1; const int8_t* nyq2;
   const double2* ph0; const double2* ph1; const double2* ph2;
@@ -199,7 +221,8 @@ struct OpTables {
 // ---------------------------------------------------------------- pass Z + operator
 __global__ void __launch_bounds__(256) k_fft_z_op(double2* __restrict__ spec, int n1, int n2, int nkx, int tx,
                                                   PlanDev pl, const double2* __restrict__ tw, OpTables T,
-                                                  SpecParams sp) {
+                                                  SpecParams sp, const double* __restrict__ done) {
+  if (done && *done != 0.0) return;
   extern __shared__ cplx sm[];
   const int cnt = 3 * tx * n2;
   cplx* a = sm;
@@ -216,7 +239,7 @@ __global__ void __launch_bounds__(256) k_fft_z_op(double2* __restrict__ spec, in
     a[(c * tx + t) * n2 + z] = cmk(v.x, v.y);
   }
   __syncthreads();
-  cplx* res = block_fft(a, b, pl, 3 * tx, tw, -1);
+  cplx* res = block_fft<-1>(a, b, pl, 3 * tx, tw);
   cplx* oth = (res == a) ? b : a;
   for (int e = threadIdx.x; e < tx * n2; e += blockDim.x) {
     const int t = e / n2, z = e - t * n2;
@@ -225,6 +248,12 @@ __global__ void __launch_bounds__(256) k_fft_z_op(double2* __restrict__ spec, in
     cplx Y0, Y1, Y2;
     if (kx >= nkx) {
       Y0 = Y1 = Y2 = cmk(0.0, 0.0);
+    } else if (sp.op == OP_LAPINV) {
+      const double sx = T.s20[kx], sy = T.s21[ky], sz = T.s22[z];
+      const double cx = T.c20[kx], cy = T.c21[ky], cz = T.c22[z];
+      const double lap = fma(sx, cy * cz, fma(cx, sy * cz, cx * cy * sz));
+      const double w = lap > 0.0 ? sp.inv_nvox / (64.0 * lap) : 0.0;
+      Y0 = cscale(X0, w); Y1 = cscale(X1, w); Y2 = cscale(X2, w);
     } else if (sp.op == OP_PROJECT) {
       if (kx == 0 && ky == 0 && z == 0) {
         if (sp.mean_out) {
@@ -270,7 +299,7 @@ __global__ void __launch_bounds__(256) k_fft_z_op(double2* __restrict__ spec, in
     oth[(2 * tx + t) * n2 + z] = Y2;
   }
   __syncthreads();
-  cplx* res2 = block_fft(oth, res, pl, 3 * tx, tw, +1);
+  cplx* res2 = block_fft<+1>(oth, res, pl, 3 * tx, tw);
   for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
     const int c = e / (tx * n2);
     const int rem = e - c * tx * n2;
@@ -284,22 +313,41 @@ __global__ void __launch_bounds__(256) k_fft_z_op(double2* __restrict__ spec, in
   }
 }
 
-int rows_per_block(int n0, int n1) {
+// Tile sizes: as large as shared memory allows (up to 1024 complex per
+// transform batch, 512 in the z pass that holds three fields), shrunk while
+// the grid would fill less than four blocks per SM, down to 256 elements.
+constexpr int FILL_BLOCKS = 4 * 152;
+
+int rows_per_block(int n0, int n1, int n2, int nf) {
   int r = 1024 / n0;
   if (r < 1) r = 1;
-  while (r > 1 && (n1 / 2) % r) --r;
   if (r > n1 / 2) r = n1 / 2;
+  while (r > 1 && (n1 / 2) % r) --r;
+  while (r > 1 && (long)(n1 / 2 / r) * n2 * nf < FILL_BLOCKS && r * n0 > 256) {
+    int q = r / 2;
+    while (q > 1 && (n1 / 2) % q) --q;
+    r = q;
+  }
   return r;
 }
-int tile_y(int n1) {
+int tile_y(int n1, int n2, int nkx, int nf) {
   int t = 1024 / n1;
   if (t > 16) t = 16;
-  return t < 1 ? 1 : t;
+  if (t < 1) t = 1;
+  while (t > 1 && (long)((nkx + t - 1) / t) * n2 * nf < FILL_BLOCKS && t * n1 > 256) t /= 2;
+  return t;
 }
-int tile_z(int n2) {
+int tile_z(int n1, int n2, int nkx, int nf) {
   int t = 512 / n2;
   if (t > 16) t = 16;
-  return t < 1 ? 1 : t;
+  if (t < 1) t = 1;
+  while (t > 1 && (long)((nkx + t - 1) / t) * n1 * (nf / 3) < FILL_BLOCKS && 3 * t * n2 > 256) t /= 2;
+  return t;
+}
+// threads for a block holding `elems` complex values (radix-4 butterflies: elems / 4)
+int threads_for(int elems) {
+  int t = (elems / 4 + 31) / 32 * 32;
+  return t < 64 ? 64 : (t > 256 ? 256 : t);
 }
 
 }  // namespace
@@ -314,53 +362,56 @@ void make_plan(int n, FFTPlan* p) {
   if (m != 1) p->npass = -1;  // unsupported length
 }
 
-cudaError_t launch_fft_forward(const rve_s* h, const double* in, cudaStream_t s) {
-  const int rpb = rows_per_block(h->n0, h->n1);
-  dim3 gx(h->n1 / 2 / rpb, h->n2, 9);
+cudaError_t launch_fft_forward(const rve_s* h, const double* in, cudaStream_t s, const double* done, int nf) {
+  const int rpb = rows_per_block(h->n0, h->n1, h->n2, nf);
+  dim3 gx(h->n1 / 2 / rpb, h->n2, nf);
   size_t shx = 2 * (size_t)rpb * h->n0 * sizeof(cplx);
   {
     ProfScope ps_(h, RVE_K_FFT_X_R2C, s);
-    k_fft_x_r2c<<<gx, 256, shx, s>>>(in, h->spec, h->n0, h->n1, h->n2, h->nkx, rpb, to_dev(h->plan[0]), h->ax[0].tw);
+    k_fft_x_r2c<<<gx, threads_for(rpb * h->n0), shx, s>>>(in, h->spec, h->n0, h->n1, h->n2, h->nkx, rpb, to_dev(h->plan[0]), h->ax[0].tw, done);
   }
-  const int ty = tile_y(h->n1);
-  dim3 gy((h->nkx + ty - 1) / ty, h->n2, 9);
+  const int ty = tile_y(h->n1, h->n2, h->nkx, nf);
+  dim3 gy((h->nkx + ty - 1) / ty, h->n2, nf);
   size_t shy = 2 * (size_t)ty * h->n1 * sizeof(cplx);
   {
     ProfScope ps_(h, RVE_K_FFT_Y, s);
-    k_fft_y<<<gy, 256, shy, s>>>(h->spec, h->n1, h->n2, h->nkx, ty, to_dev(h->plan[1]), h->ax[1].tw, -1);
+    k_fft_y<-1><<<gy, threads_for(ty * h->n1), shy, s>>>(h->spec, h->n1, h->n2, h->nkx, ty, to_dev(h->plan[1]), h->ax[1].tw, done);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_fft_op(const rve_s* h, const SpecParams& sp, cudaStream_t s) {
-  const int tz = tile_z(h->n2);
-  dim3 g((h->nkx + tz - 1) / tz, h->n1, 3);
+cudaError_t launch_fft_op(const rve_s* h, const SpecParams& sp, cudaStream_t s, const double* done, int nf) {
+  const int tz = tile_z(h->n1, h->n2, h->nkx, nf);
+  dim3 g((h->nkx + tz - 1) / tz, h->n1, nf / 3);
   size_t sh = 2 * 3 * (size_t)tz * h->n2 * sizeof(cplx);
+  const int zthreads = threads_for(3 * tz * h->n2);
   OpTables T;
   T.tan0 = h->ax[0].tanh_; T.tan1 = h->ax[1].tanh_; T.tan2 = h->ax[2].tanh_;
   T.nyq0 = h->ax[0].nyq; T.nyq1 = h->ax[1].nyq; T.nyq2 = h->ax[2].nyq;
   T.ph0 = h->ax[0].ph; T.ph1 = h->ax[1].ph; T.ph2 = h->ax[2].ph;
+  T.s20 = h->ax[0].s2; T.s21 = h->ax[1].s2; T.s22 = h->ax[2].s2;
+  T.c20 = h->ax[0].c2; T.c21 = h->ax[1].c2; T.c22 = h->ax[2].c2;
   {
     ProfScope ps_(h, RVE_K_FFT_Z_OP, s);
-    k_fft_z_op<<<g, 256, sh, s>>>(h->spec, h->n1, h->n2, h->nkx, tz, to_dev(h->plan[2]), h->ax[2].tw, T, sp);
+    k_fft_z_op<<<g, zthreads, sh, s>>>(h->spec, h->n1, h->n2, h->nkx, tz, to_dev(h->plan[2]), h->ax[2].tw, T, sp, done);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_fft_inverse(const rve_s* h, double* out, cudaStream_t s) {
-  const int ty = tile_y(h->n1);
-  dim3 gy((h->nkx + ty - 1) / ty, h->n2, 9);
+cudaError_t launch_fft_inverse(const rve_s* h, double* out, cudaStream_t s, const double* done, int nf) {
+  const int ty = tile_y(h->n1, h->n2, h->nkx, nf);
+  dim3 gy((h->nkx + ty - 1) / ty, h->n2, nf);
   size_t shy = 2 * (size_t)ty * h->n1 * sizeof(cplx);
   {
     ProfScope ps_(h, RVE_K_FFT_Y, s);
-    k_fft_y<<<gy, 256, shy, s>>>(h->spec, h->n1, h->n2, h->nkx, ty, to_dev(h->plan[1]), h->ax[1].tw, +1);
+    k_fft_y<+1><<<gy, threads_for(ty * h->n1), shy, s>>>(h->spec, h->n1, h->n2, h->nkx, ty, to_dev(h->plan[1]), h->ax[1].tw, done);
   }
-  const int rpb = rows_per_block(h->n0, h->n1);
-  dim3 gx(h->n1 / 2 / rpb, h->n2, 9);
+  const int rpb = rows_per_block(h->n0, h->n1, h->n2, nf);
+  dim3 gx(h->n1 / 2 / rpb, h->n2, nf);
   size_t shx = 2 * (size_t)rpb * h->n0 * sizeof(cplx);
   {
     ProfScope ps_(h, RVE_K_FFT_X_C2R, s);
-    k_fft_x_c2r<<<gx, 256, shx, s>>>(h->spec, out, h->n0, h->n1, h->n2, h->nkx, rpb, to_dev(h->plan[0]), h->ax[0].tw);
+    k_fft_x_c2r<<<gx, threads_for(rpb * h->n0), shx, s>>>(h->spec, out, h->n0, h->n1, h->n2, h->nkx, rpb, to_dev(h->plan[0]), h->ax[0].tw, done);
   }
   return cudaGetLastError();
 }

@@ -3,6 +3,7 @@
 // gradients on G*(K : dF) = -G*(P - Pbar) (Eq. linequil2ast), backtracking
 // on the residual norm, commit.  Every kernel runs on the caller's stream;
 // the host reads back only a few scalars per iteration.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -68,6 +69,8 @@ void carve(rve_s* h, Carver& c) {
     h->ax[a].tanh_ = c.take<double>(ns[a]);
     h->ax[a].nyq = c.take<int8_t>(ns[a]);
     h->ax[a].ph = c.take<double2>(ns[a]);
+    h->ax[a].s2 = c.take<double>(ns[a]);
+    h->ax[a].c2 = c.take<double>(ns[a]);
   }
   h->F_c = c.take<double>(9 * nv);
   h->Fp = c.take<double>(9 * nv);
@@ -213,13 +216,6 @@ rve_status read_scalars(rve_s* h) {
   return RVE_OK;
 }
 
-rve_status read_rr(rve_s* h, double* rr) {
-  RVE_CUDA(h, cudaMemcpyAsync(h->hscal + DS_RR, h->dscal + DS_RR, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  RVE_CUDA(h, cudaStreamSynchronize(h->stream));
-  if (h->prof.on) h->prof.resolve();
-  *rr = h->hscal[DS_RR];
-  return RVE_OK;
-}
 
 SpecParams project_params(const rve_s* h, const uint8_t* mask, const double* shift, double* mean_out) {
   SpecParams sp;
@@ -241,6 +237,23 @@ rve_status run_project(rve_s* h, const double* in, double* out, const SpecParams
   return RVE_OK;
 }
 
+// Y = G*(X) (minus the prescribed mean `shift` on the kept components) as
+// divergence stencil, scalar Laplace solve by FFT, gradient stencil; leaves
+// mean(X) in DS_XMEAN and sum Y^2 in DS_NORM.  Scratch: the first six
+// components of q (divergence, then the Laplace solution).
+rve_status run_project_stencil(rve_s* h, const double* X, double* Y, const uint8_t* mask, const double* shift) {
+  double* d = h->q;
+  double* u = h->q + 3 * h->nvox;
+  SpecParams sp = project_params(h, mask, nullptr, nullptr);
+  sp.op = OP_LAPINV;
+  RVE_CUDA(h, launch_div(h, X, d, 0, h->stream));
+  RVE_CUDA(h, launch_fft_forward(h, d, h->stream, nullptr, 3));
+  RVE_CUDA(h, launch_fft_op(h, sp, h->stream, nullptr, 3));
+  RVE_CUDA(h, launch_fft_inverse(h, u, h->stream, nullptr, 3));
+  RVE_CUDA(h, launch_grad(h, u, Y, mask, shift, h->stream));
+  return RVE_OK;
+}
+
 rve_status run_hardening(rve_s* h) {
   SpecParams sp = project_params(h, (const uint8_t*)"\0\0\0\0\0\0\0\0\0", nullptr, nullptr);
   sp.op = OP_CURL;
@@ -255,38 +268,48 @@ rve_status eval_residual(rve_s* h, double dt, double lambda, int out, int warm, 
                          const double* Pbar_m, double* rabs, double* scale, int* lmax, int* lfail) {
   RVE_CUDA(h, cudaMemsetAsync(h->dcount, 0, 2 * sizeof(int32_t), h->stream));
   RVE_CUDA(h, launch_constitutive(h, dt, lambda, out, warm, h->stream));
-  SpecParams sp = project_params(h, mask, Pbar_m, h->dscal + DS_MEANP);
-  RVE_TRY(run_project(h, h->P[out], h->R, sp));
-  RVE_CUDA(h, launch_norm2(h, h->R, 9, h->stream));
+  RVE_TRY(run_project_stencil(h, h->P[out], h->R, mask, Pbar_m));
   RVE_TRY(read_scalars(h));
   *rabs = std::sqrt(h->hscal[DS_NORM] / (double)h->nvox);
   double pn = 0.0;
-  for (int c = 0; c < 9; ++c) pn += h->hscal[DS_MEANP + c] * h->hscal[DS_MEANP + c];
+  for (int c = 0; c < 9; ++c) pn += h->hscal[DS_XMEAN + c] * h->hscal[DS_XMEAN + c];
   *scale = std::fmax(std::sqrt(pn), 1e-4 * h->mu);
   *lmax = h->hcount[0];
   *lfail = h->hcount[1];
   return RVE_OK;
 }
 
-// CG on G*(K : x) = -R from x = 0; returns the iteration count
-rve_status cg_solve(rve_s* h, const uint8_t* mask, int* iters, bool* ok) {
-  RVE_CUDA(h, launch_cg_init(h, h->stream));
-  double rr;
-  RVE_TRY(read_rr(h, &rr));
-  const double stop = h->opt.cg_tol * h->opt.cg_tol * rr;
+// CG on G*(K : x) = -R from x = 0 to relative residual eta.  Iterations are
+// queued in chunks; the device stops the loop itself (every CG kernel returns
+// at once after convergence), the host looks at the flag once per chunk.
+const int CG_CHUNK = 8;
+
+rve_status cg_solve(rve_s* h, const uint8_t* mask, double eta, int* iters, bool* ok) {
+  RVE_CUDA(h, launch_cg_init(h, eta, h->stream));
   SpecParams sp = project_params(h, mask, nullptr, nullptr);
-  int k = 0;
+  sp.op = OP_LAPINV;
+  const double* done = h->dscal + DS_DONE;
+  double* d = h->q;
+  double* u = h->q + 3 * h->nvox;
+  int issued = 0;
   *ok = false;
-  for (; k < h->opt.max_cg; ++k) {
-    if (rr <= stop) { *ok = true; break; }
-    RVE_CUDA(h, launch_tangent_apply(h, k == 0, h->stream));
-    RVE_TRY(run_project(h, h->t, h->q, sp));
-    RVE_CUDA(h, launch_cg_update(h, h->stream));
-    RVE_TRY(read_rr(h, &rr));
-    if (!std::isfinite(rr)) break;
+  while (issued < h->opt.max_cg) {
+    const int chunk = std::min(CG_CHUNK, h->opt.max_cg - issued);
+    for (int i = 0; i < chunk; ++i) {
+      // t = K : p, then q = G*(t) as div -> Laplace solve -> grad fused with the update
+      RVE_CUDA(h, launch_tangent_apply(h, issued + i == 0, h->stream));
+      RVE_CUDA(h, launch_div(h, h->t, d, 1, h->stream));
+      RVE_CUDA(h, launch_fft_forward(h, d, h->stream, done, 3));
+      RVE_CUDA(h, launch_fft_op(h, sp, h->stream, done, 3));
+      RVE_CUDA(h, launch_fft_inverse(h, u, h->stream, done, 3));
+      RVE_CUDA(h, launch_grad_cg(h, u, mask, h->stream));
+    }
+    issued += chunk;
+    RVE_TRY(read_scalars(h));
+    if (h->hscal[DS_DONE] != 0.0) break;
   }
-  if (!*ok && rr <= stop) *ok = true;
-  *iters = k;
+  *iters = (int)h->hscal[DS_ITERS];
+  *ok = h->hscal[DS_DONE] != 0.0 && std::isfinite(h->hscal[DS_RR]);
   return RVE_OK;
 }
 
@@ -444,12 +467,12 @@ rve_status rve_create(const int32_t* grain_id, int n0, int n1, int n2, const dou
   build_tables(*mat, q, Ap, screw);
   const int ns[3] = {n0, n1, n2};
   std::vector<double2> tw[3], ph[3];
-  std::vector<double> tn[3];
+  std::vector<double> tn[3], s2[3], c2[3];
   std::vector<int8_t> nq[3];
   const double PI = 3.14159265358979323846;
   for (int a = 0; a < 3; ++a) {
     const int n = ns[a];
-    tw[a].resize(n); ph[a].resize(n); tn[a].resize(n); nq[a].resize(n);
+    tw[a].resize(n); ph[a].resize(n); tn[a].resize(n); nq[a].resize(n); s2[a].resize(n); c2[a].resize(n);
     for (int t = 0; t < n; ++t) {
       const double ang = 2.0 * PI * (double)t / n;
       tw[a][t] = make_double2(std::cos(ang), -std::sin(ang));
@@ -458,6 +481,9 @@ rve_status rve_create(const int32_t* grain_id, int n0, int n1, int n2, const dou
       nq[a][t] = nyq ? 1 : 0;
       tn[a][t] = nyq ? 0.0 : std::tan(PI * (double)ks / n);
       ph[a][t] = nyq ? make_double2(-1.0, 0.0) : make_double2(std::cos(ang), std::sin(ang));
+      const double sh = std::sin(PI * (double)t / n), chf = std::cos(PI * (double)t / n);
+      s2[a][t] = nyq ? 1.0 : (t == 0 ? 0.0 : sh * sh);     // sin^2(xi/2), xi = 2 pi t / n
+      c2[a][t] = nyq ? 0.0 : (t == 0 ? 1.0 : chf * chf);   // cos^2(xi/2)
     }
     // exact values at the quarter points
     for (int t = 0; t < n; ++t) {
@@ -478,7 +504,9 @@ rve_status rve_create(const int32_t* grain_id, int n0, int n1, int n2, const dou
     fail_ = bad(cudaMemcpyAsync((void*)h->ax[a].tw, tw[a].data(), ns[a] * sizeof(double2), cudaMemcpyHostToDevice, s)) ||
             bad(cudaMemcpyAsync((void*)h->ax[a].tanh_, tn[a].data(), ns[a] * sizeof(double), cudaMemcpyHostToDevice, s)) ||
             bad(cudaMemcpyAsync((void*)h->ax[a].nyq, nq[a].data(), ns[a] * sizeof(int8_t), cudaMemcpyHostToDevice, s)) ||
-            bad(cudaMemcpyAsync((void*)h->ax[a].ph, ph[a].data(), ns[a] * sizeof(double2), cudaMemcpyHostToDevice, s));
+            bad(cudaMemcpyAsync((void*)h->ax[a].ph, ph[a].data(), ns[a] * sizeof(double2), cudaMemcpyHostToDevice, s)) ||
+            bad(cudaMemcpyAsync((void*)h->ax[a].s2, s2[a].data(), ns[a] * sizeof(double), cudaMemcpyHostToDevice, s)) ||
+            bad(cudaMemcpyAsync((void*)h->ax[a].c2, c2[a].data(), ns[a] * sizeof(double), cudaMemcpyHostToDevice, s));
   }
   // initial state: F = Fp = I, S = 0, rho_SSD = rho0 / 12, dF_last = 0
   if (!fail_) {
@@ -497,6 +525,7 @@ rve_status rve_create(const int32_t* grain_id, int n0, int n1, int n2, const dou
             bad(cudaMemsetAsync(h->dF_last, 0, 9 * nvox * sizeof(double), s)) ||
             bad(cudaMemsetAsync(h->nye, 0, 9 * nvox * sizeof(double), s)) ||
             bad(cudaMemsetAsync(h->dscal, 0, 64 * sizeof(double), s)) ||
+            bad(cudaMemsetAsync(h->dcount, 0, 16 * sizeof(int32_t), s)) ||
             bad(cudaStreamSynchronize(s));
   }
   if (fail_) {
@@ -556,18 +585,31 @@ rve_status rve_step(rve_t* h, const double dFbar[9], const uint8_t strain_mask[9
       return finish(fail(h, RVE_ENOCONV_NEWTON, "Newton-Raphson reached max_newton"));
     int ncg;
     bool cgok;
-    st = cg_solve(h, mask, &ncg, &cgok);
+    // inexact Newton: with cg_adaptive the linear solve only needs to be as
+    // accurate as the current residual (forcing term min(1e-2, res)); the
+    // converged increment does not depend on it
+    const double eta = h->opt.cg_adaptive ? std::fmax(h->opt.cg_tol, std::fmin(1e-2, res)) : h->opt.cg_tol;
+    st = cg_solve(h, mask, eta, &ncg, &cgok);
     if (st != RVE_OK) return finish(st);
     if (loc.newton_iters < RVE_MAX_NEWTON_LOG) loc.cg_iters[loc.newton_iters] = ncg;
     loc.cg_iters_total += ncg;
+    // backtracking on phi(lam) = rms(R(F + lam dF))^2 with sufficient decrease;
+    // after a rejected trial the next lam minimises the quadratic through
+    // phi(0), the Newton slope -2 phi(0) and phi(lam), kept in [0.1, 0.5] lam
     double lam = 1.0, rt = 0.0, sct = 0.0;
     int lm = 0, lf = 0;
     bool acc = false;
+    const double f0 = rabs * rabs;
     for (int hv = 0; hv <= h->opt.max_halvings; ++hv) {
       st = eval_residual(h, dt, lam, 1 - cur, cur, mask, Pb, &rt, &sct, &lm, &lf);
       if (st != RVE_OK) return finish(st);
-      if (lf == 0 && rt < rabs) { acc = true; break; }
-      lam *= 0.5;
+      if (lf == 0 && rt < rabs * (1.0 - 1e-4 * lam)) { acc = true; break; }
+      double next = 0.5 * lam;
+      if (lf == 0 && std::isfinite(rt)) {
+        const double c = (rt * rt - f0 * (1.0 - 2.0 * lam)) / (lam * lam);
+        if (c > 0.0) next = std::fmin(std::fmax(f0 / c, 0.1 * lam), 0.5 * lam);
+      }
+      lam = next;
       ++loc.halvings;
     }
     if (!acc) {
@@ -691,8 +733,9 @@ rve_status rve_eval_constitutive(rve_t* h, double dt, int32_t* local_max_iters, 
 
 rve_status rve_project(rve_t* h, const uint8_t strain_mask[9], const double* d_X, double* d_Y) {
   if (!h || !strain_mask || !d_X || !d_Y) return RVE_EINVAL;
-  SpecParams sp = project_params(h, strain_mask, nullptr, nullptr);
-  RVE_TRY(run_project(h, d_X, d_Y, sp));
+  uint8_t mask[9];
+  for (int c = 0; c < 9; ++c) mask[c] = strain_mask[c] ? 1 : 0;
+  RVE_TRY(run_project_stencil(h, d_X, d_Y, mask, nullptr));
   RVE_CUDA(h, cudaStreamSynchronize(h->stream));
   return RVE_OK;
 }

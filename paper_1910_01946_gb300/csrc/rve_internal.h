@@ -20,7 +20,11 @@ struct FFTPlan {
 };
 
 // Operator applied in frequency space between the forward and inverse z passes.
-enum SpecOp { OP_PROJECT = 0, OP_CURL = 1 };
+//   OP_PROJECT: 9 fields, (G X)_ij = n_j sum_l X_il n_l with the zero-mode mixed control
+//   OP_CURL:    9 fields, G_ij = -eps_jkl D_k X_il
+//   OP_LAPINV:  3 fields, each multiplied by 1 / (64 nvox sum_m s2_m prod_{j!=m} c2_j),
+//               the inverse of D^H D for the unscaled rotated-scheme stencils (0 where it vanishes)
+enum SpecOp { OP_PROJECT = 0, OP_CURL = 1, OP_LAPINV = 2 };
 
 struct SpecParams {
   int op;
@@ -37,6 +41,8 @@ struct AxisTables {
   const double* tanh_;  // tan(pi k' / n) for the frequency index k (signed k'), Nyquist: 0
   const int8_t* nyq;    // 1 at the Nyquist index of an even n
   const double2* ph;    // e^{i xi_k}, exactly -1 at Nyquist
+  const double* s2;     // sin^2(xi_k / 2)
+  const double* c2;     // cos^2(xi_k / 2)
 };
 
 struct Consts {        // material constants read by the hardening and constitutive kernels
@@ -90,7 +96,7 @@ struct rve_s {
   double2* spec;        // 9 * nspec
   double* partial;      // 4 * RVE_RED_BLOCKS
   double* dscal;        // device scalars (see DS_*)
-  int32_t* dcount;      // device counters: [0] local max iters, [1] local failures
+  int32_t* dcount;      // device counters: [0] local max iters, [1] local failures, [4] last-block ticket
   double* hscal;        // pinned host mirror of dscal
   int32_t* hcount;      // pinned host mirror of dcount
 
@@ -111,14 +117,27 @@ struct ProfScope {
 };
 
 // device scalar slots
-enum { DS_RR = 0, DS_PKP = 1, DS_ALPHA = 2, DS_BETA = 3, DS_NORM = 4, DS_MEANP = 8,
-       DS_MEANSIG = 17, DS_MEANF = 26, DS_COUNT = 40 };
+enum { DS_RR = 0, DS_PKP = 1, DS_ALPHA = 2, DS_BETA = 3, DS_NORM = 4, DS_STOP = 5, DS_DONE = 6, DS_ITERS = 7,
+       DS_MEANP = 8,
+       DS_MEANSIG = 17, DS_MEANF = 26, DS_XMEAN = 48 };
 
 // ---- fft.cu ----
-cudaError_t launch_fft_forward(const rve_s* h, const double* in, cudaStream_t s);
-cudaError_t launch_fft_op(const rve_s* h, const SpecParams& sp, cudaStream_t s);
-cudaError_t launch_fft_inverse(const rve_s* h, double* out, cudaStream_t s);
+// `done` (nullable, device): when *done != 0 every block returns at once (the
+// conjugate-gradient loop has converged on the device)
+// nf: number of fields transformed (9, or 3 for OP_LAPINV)
+cudaError_t launch_fft_forward(const rve_s* h, const double* in, cudaStream_t s, const double* done = nullptr,
+                               int nf = 9);
+cudaError_t launch_fft_op(const rve_s* h, const SpecParams& sp, cudaStream_t s, const double* done = nullptr,
+                          int nf = 9);
+cudaError_t launch_fft_inverse(const rve_s* h, double* out, cudaStream_t s, const double* done = nullptr,
+                               int nf = 9);
 void make_plan(int n, FFTPlan* p);
+
+// ---- stencil.cu: G* = D (D^H D)^-1 D^H with real-space rotated-scheme stencils ----
+cudaError_t launch_div(const rve_s* h, const double* X, double* d, int check_done, cudaStream_t s);
+cudaError_t launch_grad(const rve_s* h, const double* u, double* Y, const uint8_t* mask, const double* shift,
+                        cudaStream_t s);
+cudaError_t launch_grad_cg(const rve_s* h, const double* u, const uint8_t* mask, cudaStream_t s);
 
 // ---- constitutive.cu ----
 cudaError_t launch_hardening(const rve_s* h, cudaStream_t s);
@@ -130,7 +149,7 @@ cudaError_t launch_tangent_apply(const rve_s* h, int first, cudaStream_t s);
 cudaError_t launch_cg_update(const rve_s* h, cudaStream_t s);
 cudaError_t launch_norm2(const rve_s* h, const double* a, int ncomp, cudaStream_t s);
 cudaError_t launch_reduce_final(const rve_s* h, int mode, cudaStream_t s);
-cudaError_t launch_cg_init(const rve_s* h, cudaStream_t s);
+cudaError_t launch_cg_init(const rve_s* h, double eta, cudaStream_t s);
 cudaError_t launch_axpy_F(const rve_s* h, double lambda, cudaStream_t s);
 cudaError_t launch_predictor(const rve_s* h, const double* dFb, const double* dFb_prev, double ratio,
                              int extrapolate, cudaStream_t s);

@@ -24,12 +24,31 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return s;
 }
 
-// p = r (first) or r + beta p; t = K : p; partial of p . t
-__global__ void __launch_bounds__(RVE_RED_THREADS) k_tangent_apply(size_t nvox, const double* __restrict__ K,
-                                                                   const double* __restrict__ r, double* __restrict__ p,
-                                                                   double* __restrict__ t, const double* __restrict__ ds,
-                                                                   int first, double* __restrict__ partial) {
+// Last-block finalisation: every block has written its partial; the block
+// that takes the last ticket sums the partials in block order (deterministic)
+// and returns the total in thread 0 (other threads and blocks get NaN).
+__device__ __forceinline__ double last_block_sum(const double* partial, unsigned int* ticket, double* sh) {
+  __shared__ bool last;
+  __threadfence();
+  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return NAN;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) acc += __ldcg(partial + i);
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) *ticket = 0u;
+  return s;
+}
+
+// p = r (first) or r + beta p; t = K : p; pKp = p . t; alpha = rr / pKp.
+// Returns at once when the CG loop has converged (done != 0).
+__global__ void __launch_bounds__(RVE_RED_THREADS, 2) k_tangent_apply(size_t nvox, const double* __restrict__ K,
+                                                                      const double* __restrict__ r, double* __restrict__ p,
+                                                                      double* __restrict__ t, double* __restrict__ ds,
+                                                                      int first, double* __restrict__ partial,
+                                                                      unsigned int* __restrict__ ticket) {
   __shared__ double sh[32];
+  if (ds[DS_DONE] != 0.0) return;
   const double beta = first ? 0.0 : ds[DS_BETA];
   double acc = 0.0;
   for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (size_t)gridDim.x * blockDim.x) {
@@ -40,24 +59,39 @@ __global__ void __launch_bounds__(RVE_RED_THREADS) k_tangent_apply(size_t nvox, 
       pv[k] = first ? rv : fma(beta, p[k * nvox + v], rv);
       p[k * nvox + v] = pv[k];
     }
+    // three rows of K (27 streamed loads in flight) per stage
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      double s = 0.0;
+    for (int ib = 0; ib < 3; ++ib) {
+      double kk[27];
 #pragma unroll
-      for (int j = 0; j < 9; ++j) s = fma(K[(size_t)(9 * i + j) * nvox + v], pv[j], s);
-      t[i * nvox + v] = s;
-      acc = fma(pv[i], s, acc);
+      for (int e = 0; e < 27; ++e) kk[e] = __ldcs(K + (size_t)(27 * ib + e) * nvox + v);
+#pragma unroll
+      for (int ii = 0; ii < 3; ++ii) {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) s = fma(kk[9 * ii + j], pv[j], s);
+        t[(3 * ib + ii) * nvox + v] = s;
+        acc = fma(pv[3 * ib + ii], s, acc);
+      }
     }
   }
   const double s = block_sum(acc, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  const double tot = last_block_sum(partial, ticket, sh);
+  if (threadIdx.x == 0 && !isnan(tot)) {
+    ds[DS_PKP] = tot;
+    ds[DS_ALPHA] = ds[DS_RR] / tot;
+  }
 }
 
-// x += alpha p; r -= alpha q; partial of r . r
+// x += alpha p; r -= alpha q; rr' = r . r; beta = rr' / rr; one more
+// iteration counted; done once rr' <= stop.
 __global__ void __launch_bounds__(RVE_RED_THREADS) k_cg_update(size_t n, double* __restrict__ x, double* __restrict__ r,
                                                                const double* __restrict__ p, const double* __restrict__ q,
-                                                               const double* __restrict__ ds, double* __restrict__ partial) {
+                                                               double* __restrict__ ds, double* __restrict__ partial,
+                                                               unsigned int* __restrict__ ticket) {
   __shared__ double sh[32];
+  if (ds[DS_DONE] != 0.0) return;
   const double alpha = ds[DS_ALPHA];
   double acc = 0.0;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
@@ -68,11 +102,20 @@ __global__ void __launch_bounds__(RVE_RED_THREADS) k_cg_update(size_t n, double*
   }
   const double s = block_sum(acc, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  const double tot = last_block_sum(partial, ticket, sh);
+  if (threadIdx.x == 0 && !isnan(tot)) {
+    ds[DS_BETA] = tot / ds[DS_RR];
+    ds[DS_RR] = tot;
+    ds[DS_ITERS] += 1.0;
+    if (!(tot > ds[DS_STOP])) ds[DS_DONE] = 1.0;   // also stops on NaN
+  }
 }
 
-// x = 0; r = -R; partial of r . r
+// x = 0; r = -R; rr = r . r; stop = eta^2 rr; iteration count 0
 __global__ void __launch_bounds__(RVE_RED_THREADS) k_cg_init(size_t n, double* __restrict__ x, double* __restrict__ r,
-                                                             const double* __restrict__ R, double* __restrict__ partial) {
+                                                             const double* __restrict__ R, double* __restrict__ ds,
+                                                             double eta, double* __restrict__ partial,
+                                                             unsigned int* __restrict__ ticket) {
   __shared__ double sh[32];
   double acc = 0.0;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
@@ -83,6 +126,13 @@ __global__ void __launch_bounds__(RVE_RED_THREADS) k_cg_init(size_t n, double* _
   }
   const double s = block_sum(acc, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  const double tot = last_block_sum(partial, ticket, sh);
+  if (threadIdx.x == 0 && !isnan(tot)) {
+    ds[DS_RR] = tot;
+    ds[DS_STOP] = eta * eta * tot;
+    ds[DS_ITERS] = 0.0;
+    ds[DS_DONE] = (tot > 0.0) ? 0.0 : 1.0;
+  }
 }
 
 __global__ void __launch_bounds__(RVE_RED_THREADS) k_norm2(size_t n, const double* __restrict__ a, double* __restrict__ partial) {
@@ -269,31 +319,27 @@ cudaError_t launch_tangent_apply(const rve_s* h, int first, cudaStream_t s) {
   {
     ProfScope ps_(h, RVE_K_TANGENT_APPLY, s);
     k_tangent_apply<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, h->K[h->cur], h->r, h->p, h->t, h->dscal,
-                                                             first, h->partial);
+                                                               first, h->partial, (unsigned int*)(h->dcount + 4));
   }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  return launch_reduce_final(h, RED_PKP_ALPHA, s);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_cg_update(const rve_s* h, cudaStream_t s) {
   {
     ProfScope ps_(h, RVE_K_CG_UPDATE, s);
-    k_cg_update<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(9 * h->nvox, h->x, h->r, h->p, h->q, h->dscal, h->partial);
+    k_cg_update<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(9 * h->nvox, h->x, h->r, h->p, h->q, h->dscal, h->partial,
+                                                           (unsigned int*)(h->dcount + 4));
   }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  return launch_reduce_final(h, RED_RR_BETA, s);
+  return cudaGetLastError();
 }
 
-cudaError_t launch_cg_init(const rve_s* h, cudaStream_t s) {
+cudaError_t launch_cg_init(const rve_s* h, double eta, cudaStream_t s) {
   {
     ProfScope ps_(h, RVE_K_OTHER, s);
-    k_cg_init<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(9 * h->nvox, h->x, h->r, h->R, h->partial);
+    k_cg_init<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(9 * h->nvox, h->x, h->r, h->R, h->dscal, eta, h->partial,
+                                                         (unsigned int*)(h->dcount + 4));
   }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  return launch_reduce_final(h, RED_RR_INIT, s);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_norm2(const rve_s* h, const double* a, int ncomp, cudaStream_t s) {

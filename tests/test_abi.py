@@ -47,6 +47,6 @@ def test_workspace_bytes_validation(lib):
 def test_struct_layouts_match_header():
     import ctypes as C
     import paper_1910_01946_gb300 as pkg
-    assert C.sizeof(pkg.rve_options) == 4 * 8 + 6 * 4
+    assert C.sizeof(pkg.rve_options) == 4 * 8 + 8 * 4
     assert C.sizeof(pkg.rve_material) == 7 * 8 + 6 * 8 + 8 + 5 * 8 + 8
     assert pkg.rve_step_info.residual.offset == 24
