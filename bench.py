@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(rvegen.WORKLOADS))
+    ap.add_argument("--precision", default="f64", choices=["f64", "mixed"],
+                    help="mixed: FP32 conjugate gradients with FP64 local update and residual")
     return ap.parse_args()
 
 
@@ -104,9 +106,19 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- roofline
-def kernel_models(n0, n1, n2):
+# FP64 operations of the local update, counted from the kernel's arithmetic
+# (an FMA counts 2; constant Schmid-tensor entries 0 and +-1 folded): per voxel
+# set-up (frame rotation, trial elastic state), per residual evaluation, per
+# Newton iteration (Jacobian, LU, solve) and per voxel for the tangent.
+CONST_SETUP, CONST_EVAL, CONST_ITER, CONST_TANGENT = 180.0, 500.0, 1530.0, 8760.0
+CONST_BYTES = 364 + 864        # reads F, dF, Fp^-1, tauc, S, grain; writes P, K, S, dgam
+
+
+def kernel_models(n0, n1, n2, local=None):
     """Algorithmic FP64 flops and bytes per launch of each kernel category
-    (FFTs: 2.5 N log2 N per real and 5 N log2 N per complex transform)."""
+    (FFTs: 2.5 N log2 N per real and 5 N log2 N per complex transform).
+    `local` = (launches, local iterations, local evaluations) of the local
+    update in the timed region, for its per-launch average."""
     nvox = n0 * n1 * n2
     nkx = n0 // 2 + 1
     nspec = nkx * n1 * n2
@@ -120,12 +132,17 @@ def kernel_models(n0, n1, n2):
         "fft_z_op": (fz, 2 * 9 * nspec * 16),
         "fft_x_c2r": (fx, 9 * nvox * 8 + 9 * nspec * 16),
         "tangent_apply": (nvox * (162 + 18 + 18), nvox * (81 + 9 + 9 + 9 + 9) * 8),
-        "cg_update": (9 * nvox * 6, 9 * nvox * 5 * 8),
-    }
+        # divergence stencil 9 -> 3 fields: 3 corner differences per field + row sums + means
+        "stencil": (nvox * (9 * 7 + 6 + 9), nvox * (9 + 3) * 8),
+        # gradient stencil 3 -> 9 fused with x += alpha p, r -= alpha q, r.r
+        "cg_update": (nvox * (3 * 17 + 9 + 27 * 2), nvox * (3 + 9 * 5) * 8),
+    } | ({"constitutive": ((local[0] * nvox * (CONST_SETUP + CONST_TANGENT) + local[1] * CONST_ITER
+                            + local[2] * CONST_EVAL) / local[0], nvox * CONST_BYTES)}
+         if local and local[0] else {})
 
 
-def roofline(stats, shape, peaks):
-    models = kernel_models(*shape)
+def roofline(stats, shape, peaks, local=None):
+    models = kernel_models(*shape, local=local)
     timed = {k: v for k, v in stats.items() if v[0] > 0 and v[1] > 0}
     if not timed:
         return None, None
@@ -270,7 +287,8 @@ def main():
             dist.barrier()
 
     # ---- device-resident run (inputs already on the GPU)
-    rve = pkg.RVE(gid, quat, mat, wl.edge, device=dev)
+    prec = 1 if a.precision == "mixed" else 0
+    rve = pkg.RVE(gid, quat, mat, wl.edge, device=dev, precision=prec)
     stream = rve.stream
     for _ in range(a.warmup):
         rve.step(wl.dFbar(), mask, Pbar, wl.dt)
@@ -284,10 +302,13 @@ def main():
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     cg_total, newton_total, evals = 0, 0, 0
+    local_iters, local_evals = 0, 0
     for _ in range(a.steps):
         info = rve.step(wl.dFbar(), mask, Pbar, wl.dt)
         cg_total += info["cg_iters_total"]
         newton_total += info["newton_iters"]
+        local_iters += info["local_iters_total"]
+        local_evals += info["local_evals_total"]
     ev1.record(stream)
     barrier()
     clocks.stop()
@@ -314,7 +335,7 @@ def main():
         sig_h = torch.empty((9, nvox), dtype=torch.float64).pin_memory()
         gnd_h = torch.empty((12, nvox), dtype=torch.float64).pin_memory()
         load_h = torch.empty(9 + 9, dtype=torch.float64).pin_memory().numpy()
-        r2 = pkg.RVE(gid, quat, mat, wl.edge, device=dev)
+        r2 = pkg.RVE(gid, quat, mat, wl.edge, device=dev, precision=prec)
         cg2 = 0
         h2d = 9 * 8 + 9 + 9 * 8
         d2h = sig_h.numel() * 8 + gnd_h.numel() * 8 + 2 * 9 * 8
@@ -351,7 +372,7 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return
-    dom, roof = roofline(stats, (wl.n, wl.n, wl.n), peaks)
+    dom, roof = roofline(stats, (wl.n, wl.n, wl.n), peaks, local=(evals, local_iters, local_evals))
     roof_line = None
     if roof is not None and "bound" in roof:
         roof_line = {"bound": roof["bound"], "achieved": roof["achieved"], "peak": roof["peak"], "unit": roof["unit"],
@@ -371,13 +392,17 @@ def main():
                          f"this run's {evals_per_inc:.1f} evaluations and {cg_per_inc:.0f} CG iterations per increment"}
     line = {"metric": "voxel-iterations/s", "value": value, "unit": "voxel-iter/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == 0 else "f64 local update and residual, f32 conjugate gradients",
+            "data": "synthetic", "config": config,
             "e2e": e2e, "gpu_launches": launches, "roofline": roof_line, "cpu_baseline": cpu,
             "clocks": clocks.summary(),
             "detail": {"voxel_increments_per_s": world * nvox * a.steps / (ms_max / 1e3),
                        "cg_iters_per_increment": cg_total / a.steps,
                        "newton_iters_per_increment": newton_total / a.steps,
                        "local_evals_per_increment": evals / a.steps,
+                       "local_newton_iters_per_voxel_eval": local_iters / max(1, evals * nvox),
+                       "local_residual_evals_per_voxel_eval": local_evals / max(1, evals * nvox),
                        "macro_P11_MPa": float(P_macro[0, 0]), "macro_sigma11_MPa": float(sig_macro[0, 0]),
                        "kernels_ms": {k: round(v[1], 3) for k, v in stats.items()},
                        "kernels_launches": {k: v[0] for k, v in stats.items()}}}

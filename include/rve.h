@@ -80,7 +80,10 @@ typedef struct {
   double local_tol;      /* local update: max |r| <= local_tol * mu */
   int32_t max_newton, max_cg, max_local, max_halvings;
   int32_t extrapolate;   /* nonzero: predict the increment from the previous one */
-  int32_t precision;     /* 0: FP64 throughout (the only value accepted) */
+  int32_t precision;     /* 0: FP64 throughout.  1: mixed -- the conjugate gradients (tangent storage,
+                            stencils, FFT, vectors) in FP32; the local update, tangent computation,
+                            equilibrium residual and Newton update in FP64, so the converged
+                            increment is the FP64 one (outer Newton refinement) */
   int32_t cg_adaptive;   /* nonzero: CG relative tolerance max(cg_tol, min(1e-2, current relative
                             residual)) (inexact Newton; the converged increment is the same) */
 } rve_options;
@@ -93,6 +96,8 @@ typedef struct {
   int32_t local_max_iters;
   int32_t local_failures;
   int32_t halvings;
+  int64_t local_iters_total;                    /* local Newton iterations summed over voxels and evaluations */
+  int64_t local_evals_total;                    /* local residual evaluations, likewise */
   double residual;                              /* final relative residual */
   double seconds;                               /* host wall time of the call */
   int32_t cg_iters[RVE_MAX_NEWTON_LOG];         /* per Newton iteration */
@@ -123,9 +128,9 @@ enum {
 };
 
 /* Bytes of device workspace needed for an n0 x n1 x n2 grid of n_grains
- * grains.  n0 and n1 must be even, every size a product of 2s and 3s with
- * 2 <= n0, n1 <= 512 and 1 <= n2 <= 512.  Returns 0 for unsupported sizes,
- * grain counts or precision. */
+ * grains at the given precision (rve_options.precision).  n0 and n1 must be
+ * even, every size a product of 2s and 3s with 2 <= n0, n1 <= 512 and
+ * 1 <= n2 <= 512.  Returns 0 for unsupported sizes, grain counts or precision. */
 size_t rve_workspace_bytes(int n0, int n1, int n2, int n_grains, int precision);
 
 /* Create a handle.

@@ -50,6 +50,7 @@ class rve_options(C.Structure):
 class rve_step_info(C.Structure):
     _fields_ = [("converged", C.c_int32), ("newton_iters", C.c_int32), ("cg_iters_total", C.c_int32),
                 ("local_max_iters", C.c_int32), ("local_failures", C.c_int32), ("halvings", C.c_int32),
+                ("local_iters_total", C.c_int64), ("local_evals_total", C.c_int64),
                 ("residual", C.c_double), ("seconds", C.c_double), ("cg_iters", C.c_int32 * MAX_NEWTON_LOG),
                 ("residuals", C.c_double * (MAX_NEWTON_LOG + 1))]
 
@@ -264,6 +265,7 @@ class RVE:
                    cg_iters=list(info.cg_iters[:min(info.newton_iters, MAX_NEWTON_LOG)]),
                    cg_iters_total=info.cg_iters_total, local_max_iters=info.local_max_iters,
                    local_failures=info.local_failures, halvings=info.halvings, residual=info.residual,
+                   local_iters_total=info.local_iters_total, local_evals_total=info.local_evals_total,
                    residuals=list(info.residuals[:min(info.newton_iters, MAX_NEWTON_LOG) + 1]),
                    seconds=info.seconds)
         if check:

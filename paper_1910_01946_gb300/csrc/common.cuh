@@ -78,16 +78,22 @@ RVE_HD double mat3_inv(const double* A, double* B) {
 }
 
 // ---- deterministic reductions shared by the reducing kernels ----
-// block-wide sum, result in thread 0 (all threads must call it)
+// linear thread index and block size (1-D or 2-D blocks)
+__device__ __forceinline__ int lin_tid() { return threadIdx.x + blockDim.x * threadIdx.y; }
+__device__ __forceinline__ int lin_nthreads() { return blockDim.x * blockDim.y; }
+
+// block-wide sum, result in linear thread 0 (all threads must call it; the
+// block size is a multiple of 32)
 __device__ __forceinline__ double blk_sum(double v, double* sh) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int t = lin_tid();
+  const int lane = t & 31, wid = t >> 5;
   if (lane == 0) sh[wid] = v;
   __syncthreads();
   double s = 0.0;
-  if (threadIdx.x == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
+  if (t == 0) {
+    const int nw = (lin_nthreads() + 31) >> 5;
     for (int w = 0; w < nw; ++w) s += sh[w];
   }
   __syncthreads();
@@ -101,17 +107,18 @@ __device__ __forceinline__ double blk_sum(double v, double* sh) {
 __device__ __forceinline__ bool last_block_sums(const double* partial, int nval, unsigned int* ticket, double* sh,
                                                 double* out) {
   __shared__ bool last;
+  const int t = lin_tid();
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  if (t == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
   __syncthreads();
   if (!last) return false;
   for (int c = 0; c < nval; ++c) {
     double acc = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) acc += __ldcg(partial + (size_t)c * gridDim.x + i);
+    for (int i = t; i < (int)gridDim.x; i += lin_nthreads()) acc += __ldcg(partial + (size_t)c * gridDim.x + i);
     const double s = blk_sum(acc, sh);
-    if (threadIdx.x == 0) out[c] = s;
+    if (t == 0) out[c] = s;
   }
-  if (threadIdx.x == 0) *ticket = 0u;
+  if (t == 0) *ticket = 0u;
   return true;
 }

@@ -275,9 +275,9 @@ __global__ void __launch_bounds__(128) k_constitutive(
     const double* __restrict__ Fin, const double* __restrict__ xdir, double lambda,
     const double* __restrict__ Fp0inv, const double* __restrict__ tauc_g, const double* __restrict__ Swarm,
     double* __restrict__ Pout, double* __restrict__ Kout, double* __restrict__ Sout, double* __restrict__ dgout,
-    int32_t* __restrict__ counters, double dt, Consts c) {
+    int32_t* __restrict__ counters, double dt, Consts c, int k32) {
   const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int iters = 0, failed = 0;
+  int iters = 0, failed = 0, evals = 0;
   if (v < nvox) {
     double R[9], Fs[9], T[9], Ft[9], Fpi0[9];
     const int g = grain[v];
@@ -304,10 +304,12 @@ __global__ void __launch_bounds__(128) k_constitutive(
 
     Eval e;
     evaluate(c, S, A, tauc, dt, e);
+    ++evals;
     if (!(e.rn < INFINITY)) {             // warm start rejected: restart from the elastic-free state
 #pragma unroll
       for (int k = 0; k < 6; ++k) S[k] = 0.0;
       evaluate(c, S, A, tauc, dt, e);
+      ++evals;
     }
     double J[36], dgp[12];
     int piv[6];
@@ -327,6 +329,7 @@ __global__ void __launch_bounds__(128) k_constitutive(
         for (int k = 0; k < 6; ++k) St[k] = fma(lam, d[k], S[k]);
         Eval et;
         evaluate(c, St, A, tauc, dt, et);
+        ++evals;
         if (et.rn < e.rn) {
 #pragma unroll
           for (int k = 0; k < 6; ++k) S[k] = St[k];
@@ -411,16 +414,27 @@ __global__ void __launch_bounds__(128) k_constitutive(
       mat3_mult(dPt, R, U);
       mat3_mul(R, U, dP);
 #pragma unroll
-      for (int ij = 0; ij < 9; ++ij) Kout[(size_t)(9 * ij + kl) * nvox + v] = dP[ij];
+      for (int ij = 0; ij < 9; ++ij) {
+        if (k32)   // mixed precision: the tangent only drives the FP32 conjugate gradients
+          reinterpret_cast<float*>(Kout)[(size_t)(9 * ij + kl) * nvox + v] = (float)dP[ij];
+        else
+          Kout[(size_t)(9 * ij + kl) * nvox + v] = dP[ij];
+      }
     }
   }
   // counters: warp-aggregated
   const unsigned full = 0xffffffffu;
   int mx = __reduce_max_sync(full, iters);
   int nf = __reduce_add_sync(full, failed);
+  unsigned si = __reduce_add_sync(full, (unsigned)iters);
+  unsigned se = __reduce_add_sync(full, (unsigned)evals);
   if ((threadIdx.x & 31) == 0) {
     if (mx) atomicMax(&counters[0], mx);
     if (nf) atomicAdd(&counters[1], nf);
+    // 64-bit totals of local Newton iterations and residual evaluations (work accounting)
+    unsigned long long* tot = reinterpret_cast<unsigned long long*>(counters + 8);
+    atomicAdd(&tot[0], (unsigned long long)si);
+    atomicAdd(&tot[1], (unsigned long long)se);
   }
 }
 
@@ -444,7 +458,7 @@ cudaError_t launch_constitutive(const rve_s* h, double dt, double lambda, int ou
     ProfScope ps_(h, RVE_K_CONSTITUTIVE, s);
     k_constitutive<<<blocks, 128, 0, s>>>(h->nvox, h->grain, h->grainR, h->F, h->x, lambda, h->Fp0inv, h->tauc,
                                         warm, h->P[out_buf], h->K[out_buf], h->S[out_buf], h->dgam[out_buf],
-                                        h->dcount, dt, h->cst);
+                                        h->dcount, dt, h->cst, h->opt.precision == 1);
   }
   return cudaGetLastError();
 }

@@ -1,5 +1,5 @@
-// Hand-written batched 3-D real FFT of the nine tensor-component fields
-// (FP64), with the frequency-space operators of the method fused between the
+// Hand-written batched 3-D real FFT of tensor-component fields (FP64, and
+// FP32 for the mixed-precision conjugate gradients), with the frequency-space operators of the method fused between the
 // forward and inverse transforms along z:
 //   - the Galerkin projection with mixed control (Sec. 2.2, Eqs. weakarbi,
 //     eql_discrete2) built from the rotated-scheme frequencies (App. A, Eq. kas);
@@ -21,6 +21,19 @@
 
 namespace {
 
+// complex value and storage pair type of a real type R (double or float)
+template <typename R> struct CX { R x, y; };
+template <typename R> struct V2T;
+template <> struct V2T<double> { typedef double2 t; };
+template <> struct V2T<float> { typedef float2 t; };
+template <typename R> using V2 = typename V2T<R>::t;
+
+template <typename R> __device__ __forceinline__ CX<R> mk(R a, R b) { CX<R> c; c.x = a; c.y = b; return c; }
+template <typename R> __device__ __forceinline__ CX<R> add(CX<R> a, CX<R> b) { return mk<R>(a.x + b.x, a.y + b.y); }
+template <typename R> __device__ __forceinline__ CX<R> sub(CX<R> a, CX<R> b) { return mk<R>(a.x - b.x, a.y - b.y); }
+template <typename R> __device__ __forceinline__ CX<R> scl(CX<R> a, R s) { return mk<R>(a.x * s, a.y * s); }
+template <typename R> __device__ __forceinline__ V2<R> st2(R a, R b) { V2<R> v; v.x = a; v.y = b; return v; }
+
 struct PlanDev {
   int n, npass;
   int radix[RVE_MAX_RADIX_PASSES];
@@ -34,29 +47,25 @@ PlanDev to_dev(const FFTPlan& p) {
   return d;
 }
 
-template <int SIGN>
-__device__ __forceinline__ cplx ld_tw(const double2* tw, int idx) {
-  double2 w = __ldg(tw + idx);
-  return cmk(w.x, SIGN < 0 ? w.y : -w.y);
+// a * w or a * conj(w) (w from the forward table) with the sign fixed at
+// compile time, so the negation folds into the FMA operands; float
+// transforms read the float table
+template <int SIGN, typename R>
+__device__ __forceinline__ CX<R> twiddle(CX<R> a, const V2<R>* tw, int idx) {
+  const V2<R> w = __ldg(tw + idx);
+  if (SIGN < 0) return mk<R>(fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x));
+  return mk<R>(fma(a.x, w.x, a.y * w.y), fma(a.y, w.x, -a.x * w.y));
 }
 
-// a * conj-or-not(w) with the sign fixed at compile time, so the negation
-// folds into the FMA operands
-template <int SIGN>
-__device__ __forceinline__ cplx twiddle(cplx a, const double2* tw, int idx) {
-  const double2 w = __ldg(tw + idx);
-  if (SIGN < 0) return cmk(fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x));
-  return cmk(fma(a.x, w.x, a.y * w.y), fma(a.y, w.x, -a.x * w.y));
-}
-
-template <int SIGN>
-__device__ __forceinline__ cplx mul_i(cplx a) { return SIGN > 0 ? cmk(-a.y, a.x) : cmk(a.y, -a.x); }
+template <int SIGN, typename R>
+__device__ __forceinline__ CX<R> mul_i(CX<R> a) { return SIGN > 0 ? mk<R>(-a.y, a.x) : mk<R>(a.y, -a.x); }
 
 // One Stockham pass of radix R over `howmany` contiguous transforms of length
 // N from src to dst (both shared memory).
-template <int SIGN>
-__device__ void stockham_pass(const cplx* __restrict__ src, cplx* __restrict__ dst, int N, int howmany,
-                              int R, int Ns, const double2* tw) {
+template <int SIGN, typename RT>
+__device__ void stockham_pass(const CX<RT>* __restrict__ src, CX<RT>* __restrict__ dst, int N, int howmany,
+                              int R, int Ns, const V2<RT>* tw) {
+  typedef CX<RT> cplx;
   const int nb = N / R;
   const int total = nb * howmany;
   const int twstep = N / (Ns * R);
@@ -70,109 +79,116 @@ __device__ void stockham_pass(const cplx* __restrict__ src, cplx* __restrict__ d
     if (R == 4) {
       cplx a0 = X[j], a1 = X[j + nb], a2 = X[j + 2 * nb], a3 = X[j + 3 * nb];
       if (k) {
-        a1 = twiddle<SIGN>(a1, tw, k * twstep);
-        a2 = twiddle<SIGN>(a2, tw, 2 * k * twstep);
-        a3 = twiddle<SIGN>(a3, tw, 3 * k * twstep);
+        a1 = twiddle<SIGN, RT>(a1, tw, k * twstep);
+        a2 = twiddle<SIGN, RT>(a2, tw, 2 * k * twstep);
+        a3 = twiddle<SIGN, RT>(a3, tw, 3 * k * twstep);
       }
-      cplx t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = mul_i<SIGN>(csub(a1, a3));
-      Y[d] = cadd(t0, t2);
-      Y[d + Ns] = cadd(t1, t3);
-      Y[d + 2 * Ns] = csub(t0, t2);
-      Y[d + 3 * Ns] = csub(t1, t3);
+      cplx t0 = add(a0, a2), t1 = sub(a0, a2), t2 = add(a1, a3), t3 = mul_i<SIGN, RT>(sub(a1, a3));
+      Y[d] = add(t0, t2);
+      Y[d + Ns] = add(t1, t3);
+      Y[d + 2 * Ns] = sub(t0, t2);
+      Y[d + 3 * Ns] = sub(t1, t3);
     } else if (R == 2) {
       cplx a0 = X[j], a1 = X[j + nb];
-      if (k) a1 = twiddle<SIGN>(a1, tw, k * twstep);
-      Y[d] = cadd(a0, a1);
-      Y[d + Ns] = csub(a0, a1);
+      if (k) a1 = twiddle<SIGN, RT>(a1, tw, k * twstep);
+      Y[d] = add(a0, a1);
+      Y[d + Ns] = sub(a0, a1);
     } else {  // R == 3
       cplx a0 = X[j], a1 = X[j + nb], a2 = X[j + 2 * nb];
       if (k) {
-        a1 = twiddle<SIGN>(a1, tw, k * twstep);
-        a2 = twiddle<SIGN>(a2, tw, 2 * k * twstep);
+        a1 = twiddle<SIGN, RT>(a1, tw, k * twstep);
+        a2 = twiddle<SIGN, RT>(a2, tw, 2 * k * twstep);
       }
-      const double s3 = 0.86602540378443864676;  // sqrt(3)/2
-      cplx t = cadd(a1, a2);
-      cplx u = cscale(mul_i<SIGN>(csub(a1, a2)), s3);
-      cplx m = cmk(fma(-0.5, t.x, a0.x), fma(-0.5, t.y, a0.y));
-      Y[d] = cadd(a0, t);
-      Y[d + Ns] = cadd(m, u);
-      Y[d + 2 * Ns] = csub(m, u);
+      const RT s3 = (RT)0.86602540378443864676;  // sqrt(3)/2
+      cplx t = add(a1, a2);
+      cplx u = scl(mul_i<SIGN, RT>(sub(a1, a2)), s3);
+      cplx m = mk<RT>(fma((RT)-0.5, t.x, a0.x), fma((RT)-0.5, t.y, a0.y));
+      Y[d] = add(a0, t);
+      Y[d + Ns] = add(m, u);
+      Y[d + 2 * Ns] = sub(m, u);
     }
   }
 }
 
 // Full transform of `howmany` contiguous length-N sequences; the caller has
 // synchronised after filling `a`.  Returns the buffer that holds the result.
-template <int SIGN>
-__device__ cplx* block_fft(cplx* a, cplx* b, const PlanDev& pl, int howmany, const double2* tw) {
+template <int SIGN, typename RT>
+__device__ CX<RT>* block_fft(CX<RT>* a, CX<RT>* b, const PlanDev& pl, int howmany, const V2<RT>* tw) {
   int Ns = 1;
   for (int p = 0; p < pl.npass; ++p) {
     const int R = pl.radix[p];
-    stockham_pass<SIGN>(a, b, pl.n, howmany, R, Ns, tw);
+    stockham_pass<SIGN, RT>(a, b, pl.n, howmany, R, Ns, tw);
     __syncthreads();
-    cplx* t = a; a = b; b = t;
+    CX<RT>* t = a; a = b; b = t;
     Ns *= R;
   }
   return a;
 }
 
 // ---------------------------------------------------------------- pass X (R2C)
-__global__ void __launch_bounds__(256) k_fft_x_r2c(const double* __restrict__ in, double2* __restrict__ spec,
+// in: real fields (type R); spec: half spectrum (pairs of R)
+template <typename R>
+__global__ void __launch_bounds__(256) k_fft_x_r2c(const R* __restrict__ in, V2<R>* __restrict__ spec,
                                                    int n0, int n1, int n2, int nkx, int rpb, PlanDev pl,
-                                                   const double2* __restrict__ tw, const double* __restrict__ done) {
+                                                   const V2<R>* __restrict__ tw, const double* __restrict__ done) {
+  typedef CX<R> cplx;
   if (done && *done != 0.0) return;
-  extern __shared__ cplx sm[];
-  cplx* a = sm;
-  cplx* b = sm + rpb * n0;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx* a = reinterpret_cast<cplx*>(smraw);
+  cplx* b = a + rpb * n0;
   const int f = blockIdx.z, z = blockIdx.y, j0 = blockIdx.x * rpb;
   const size_t nvox = (size_t)n0 * n1 * n2;
-  const double* src = in + f * nvox + (size_t)z * n1 * n0;
+  const R* src = in + f * nvox + (size_t)z * n1 * n0;
   for (int e = threadIdx.x; e < rpb * n0; e += blockDim.x) {
     const int jj = e / n0, x = e - jj * n0;
     const int y0 = 2 * (j0 + jj);
-    a[e] = cmk(src[(size_t)y0 * n0 + x], src[(size_t)(y0 + 1) * n0 + x]);
+    a[e] = mk<R>(src[(size_t)y0 * n0 + x], src[(size_t)(y0 + 1) * n0 + x]);
   }
   __syncthreads();
-  cplx* res = block_fft<-1>(a, b, pl, rpb, tw);
-  double2* dst = spec + ((size_t)f * n2 + z) * n1 * nkx;
+  cplx* res = block_fft<-1, R>(a, b, pl, rpb, tw);
+  V2<R>* dst = spec + ((size_t)f * n2 + z) * n1 * nkx;
+  const R half = (R)0.5;
   for (int e = threadIdx.x; e < rpb * nkx; e += blockDim.x) {
     const int jj = e / nkx, k = e - jj * nkx;
     const cplx zk = res[jj * n0 + k];
-    const cplx zm = cconj(res[jj * n0 + (k == 0 ? 0 : n0 - k)]);
-    const cplx s = cadd(zk, zm), d = csub(zk, zm);
+    const cplx zc = res[jj * n0 + (k == 0 ? 0 : n0 - k)];
+    const cplx zm = mk<R>(zc.x, -zc.y);
+    const cplx s = add(zk, zm), d = sub(zk, zm);
     const int y0 = 2 * (j0 + jj);
-    dst[(size_t)y0 * nkx + k] = make_double2(0.5 * s.x, 0.5 * s.y);
-    dst[(size_t)(y0 + 1) * nkx + k] = make_double2(0.5 * d.y, -0.5 * d.x);
+    dst[(size_t)y0 * nkx + k] = st2<R>(half * s.x, half * s.y);
+    dst[(size_t)(y0 + 1) * nkx + k] = st2<R>(half * d.y, -half * d.x);
   }
 }
 
 // ---------------------------------------------------------------- pass X^-1 (C2R)
-__global__ void __launch_bounds__(256) k_fft_x_c2r(const double2* __restrict__ spec, double* __restrict__ out,
+template <typename R>
+__global__ void __launch_bounds__(256) k_fft_x_c2r(const V2<R>* __restrict__ spec, R* __restrict__ out,
                                                    int n0, int n1, int n2, int nkx, int rpb, PlanDev pl,
-                                                   const double2* __restrict__ tw, const double* __restrict__ done) {
+                                                   const V2<R>* __restrict__ tw, const double* __restrict__ done) {
+  typedef CX<R> cplx;
   if (done && *done != 0.0) return;
-  extern __shared__ cplx sm[];
-  cplx* a = sm;
-  cplx* b = sm + rpb * n0;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx* a = reinterpret_cast<cplx*>(smraw);
+  cplx* b = a + rpb * n0;
   const int f = blockIdx.z, z = blockIdx.y, j0 = blockIdx.x * rpb;
   const size_t nvox = (size_t)n0 * n1 * n2;
-  const double2* src = spec + ((size_t)f * n2 + z) * n1 * nkx;
+  const V2<R>* src = spec + ((size_t)f * n2 + z) * n1 * nkx;
   for (int e = threadIdx.x; e < rpb * n0; e += blockDim.x) {
     const int jj = e / n0, k = e - jj * n0;
     const int y0 = 2 * (j0 + jj);
     cplx A, B;
     if (k < nkx) {
-      double2 u = src[(size_t)y0 * nkx + k], v = src[(size_t)(y0 + 1) * nkx + k];
-      A = cmk(u.x, u.y); B = cmk(v.x, v.y);
+      V2<R> u = src[(size_t)y0 * nkx + k], v = src[(size_t)(y0 + 1) * nkx + k];
+      A = mk<R>(u.x, u.y); B = mk<R>(v.x, v.y);
     } else {
-      double2 u = src[(size_t)y0 * nkx + (n0 - k)], v = src[(size_t)(y0 + 1) * nkx + (n0 - k)];
-      A = cmk(u.x, -u.y); B = cmk(v.x, -v.y);
+      V2<R> u = src[(size_t)y0 * nkx + (n0 - k)], v = src[(size_t)(y0 + 1) * nkx + (n0 - k)];
+      A = mk<R>(u.x, -u.y); B = mk<R>(v.x, -v.y);
     }
-    a[e] = cmk(A.x - B.y, A.y + B.x);  // A + i B
+    a[e] = mk<R>(A.x - B.y, A.y + B.x);  // A + i B
   }
   __syncthreads();
-  cplx* res = block_fft<+1>(a, b, pl, rpb, tw);
-  double* dst = out + f * nvox + (size_t)z * n1 * n0;
+  cplx* res = block_fft<+1, R>(a, b, pl, rpb, tw);
+  R* dst = out + f * nvox + (size_t)z * n1 * n0;
   for (int e = threadIdx.x; e < rpb * n0; e += blockDim.x) {
     const int jj = e / n0, x = e - jj * n0;
     const int y0 = 2 * (j0 + jj);
@@ -182,30 +198,31 @@ __global__ void __launch_bounds__(256) k_fft_x_c2r(const double2* __restrict__ s
 }
 
 // ---------------------------------------------------------------- pass Y (C2C)
-template <int SIGN>
-__global__ void __launch_bounds__(256) k_fft_y(double2* __restrict__ spec, int n1, int n2, int nkx, int tx,
-                                               PlanDev pl, const double2* __restrict__ tw,
+template <int SIGN, typename R>
+__global__ void __launch_bounds__(256) k_fft_y(V2<R>* __restrict__ spec, int n1, int n2, int nkx, int tx,
+                                               PlanDev pl, const V2<R>* __restrict__ tw,
                                                const double* __restrict__ done) {
+  typedef CX<R> cplx;
   if (done && *done != 0.0) return;
-  extern __shared__ cplx sm[];
-  cplx* a = sm;
-  cplx* b = sm + tx * n1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx* a = reinterpret_cast<cplx*>(smraw);
+  cplx* b = a + tx * n1;
   const int f = blockIdx.z, z = blockIdx.y, kx0 = blockIdx.x * tx;
-  double2* base = spec + ((size_t)f * n2 + z) * n1 * nkx;
+  V2<R>* base = spec + ((size_t)f * n2 + z) * n1 * nkx;
   for (int e = threadIdx.x; e < tx * n1; e += blockDim.x) {
     const int y = e / tx, t = e - y * tx;
     const int kx = kx0 + t;
-    double2 v = kx < nkx ? base[(size_t)y * nkx + kx] : make_double2(0.0, 0.0);
-    a[t * n1 + y] = cmk(v.x, v.y);
+    V2<R> v = kx < nkx ? base[(size_t)y * nkx + kx] : st2<R>((R)0, (R)0);
+    a[t * n1 + y] = mk<R>(v.x, v.y);
   }
   __syncthreads();
-  cplx* res = block_fft<SIGN>(a, b, pl, tx, tw);
+  cplx* res = block_fft<SIGN, R>(a, b, pl, tx, tw);
   for (int e = threadIdx.x; e < tx * n1; e += blockDim.x) {
     const int y = e / tx, t = e - y * tx;
     const int kx = kx0 + t;
     if (kx < nkx) {
       cplx v = res[t * n1 + y];
-      base[(size_t)y * nkx + kx] = make_double2(v.x, v.y);
+      base[(size_t)y * nkx + kx] = st2<R>(v.x, v.y);
     }
   }
 }
@@ -218,15 +235,78 @@ struct OpTables {
   const double2* ph0; const double2* ph1; const double2* ph2;
 };
 
+// Operator at one frequency on the three fields of a tensor row (in double).
+__device__ __forceinline__ void apply_op(const OpTables& T, const SpecParams& sp, int i, int kx, int ky, int kz,
+                                         cplx& X0, cplx& X1, cplx& X2) {
+  cplx Y0, Y1, Y2;
+  if (sp.op == OP_LAPINV) {
+    const double sx = T.s20[kx], sy = T.s21[ky], sz = T.s22[kz];
+    const double cx = T.c20[kx], cy = T.c21[ky], cz = T.c22[kz];
+    const double lap = fma(sx, cy * cz, fma(cx, sy * cz, cx * cy * sz));
+    const double w = lap > 0.0 ? sp.inv_nvox / (64.0 * lap) : 0.0;
+    Y0 = cscale(X0, w); Y1 = cscale(X1, w); Y2 = cscale(X2, w);
+  } else if (sp.op == OP_PROJECT) {
+    if (kx == 0 && ky == 0 && kz == 0) {
+      if (sp.mean_out) {
+        sp.mean_out[3 * i + 0] = X0.x * sp.inv_nvox;
+        sp.mean_out[3 * i + 1] = X1.x * sp.inv_nvox;
+        sp.mean_out[3 * i + 2] = X2.x * sp.inv_nvox;
+      }
+      const double nv = 1.0 / sp.inv_nvox;
+      Y0 = sp.keep[3 * i + 0] ? cmk((X0.x - nv * sp.shift[3 * i + 0]) * sp.inv_nvox, X0.y * sp.inv_nvox) : cmk(0.0, 0.0);
+      Y1 = sp.keep[3 * i + 1] ? cmk((X1.x - nv * sp.shift[3 * i + 1]) * sp.inv_nvox, X1.y * sp.inv_nvox) : cmk(0.0, 0.0);
+      Y2 = sp.keep[3 * i + 2] ? cmk((X2.x - nv * sp.shift[3 * i + 2]) * sp.inv_nvox, X2.y * sp.inv_nvox) : cmk(0.0, 0.0);
+    } else {
+      const int q0 = T.nyq0[kx], q1 = T.nyq1[ky], q2 = T.nyq2[kz];
+      double u0, u1, u2;
+      if (q0 + q1 + q2 >= 2) {
+        u0 = u1 = u2 = 0.0;
+      } else if (q0 + q1 + q2 == 1) {
+        u0 = q0; u1 = q1; u2 = q2;
+      } else {
+        const double t0 = T.tan0[kx], t1 = T.tan1[ky], t2 = T.tan2[kz];
+        const double inv = rsqrt(fma(t0, t0, fma(t1, t1, t2 * t2)));
+        u0 = t0 * inv; u1 = t1 * inv; u2 = t2 * inv;
+      }
+      // (G X)_ij = u_j sum_l X_il u_l  (scaled by 1/nvox)
+      cplx s = cmk(fma(X0.x, u0, fma(X1.x, u1, X2.x * u2)), fma(X0.y, u0, fma(X1.y, u1, X2.y * u2)));
+      s = cscale(s, sp.inv_nvox);
+      Y0 = cscale(s, u0); Y1 = cscale(s, u1); Y2 = cscale(s, u2);
+    }
+  } else {  // OP_CURL: G_ij = -eps_jkl D_k Fp_il
+    const double2 e0 = T.ph0[kx], e1 = T.ph1[ky], e2 = T.ph2[kz];
+    const cplx p0 = cmk(1.0 + e0.x, e0.y), p1 = cmk(1.0 + e1.x, e1.y), p2 = cmk(1.0 + e2.x, e2.y);
+    const cplx m0 = cmk(e0.x - 1.0, e0.y), m1 = cmk(e1.x - 1.0, e1.y), m2 = cmk(e2.x - 1.0, e2.y);
+    const double sc = sp.inv4h * sp.inv_nvox;
+    const cplx D0 = cscale(cmul(m0, cmul(p1, p2)), sc);
+    const cplx D1 = cscale(cmul(p0, cmul(m1, p2)), sc);
+    const cplx D2 = cscale(cmul(p0, cmul(p1, m2)), sc);
+    Y0 = csub(cmul(D2, X1), cmul(D1, X2));
+    Y1 = csub(cmul(D0, X2), cmul(D2, X0));
+    Y2 = csub(cmul(D1, X0), cmul(D0, X1));
+  }
+  X0 = Y0; X1 = Y1; X2 = Y2;
+}
+
+// inverse-Laplacian weight in float for the float path
+__device__ __forceinline__ float lapinv_weight_f(const OpTables& T, float inv_nvox, int kx, int ky, int kz) {
+  const float sx = (float)T.s20[kx], sy = (float)T.s21[ky], sz = (float)T.s22[kz];
+  const float cx = (float)T.c20[kx], cy = (float)T.c21[ky], cz = (float)T.c22[kz];
+  const float lap = fmaf(sx, cy * cz, fmaf(cx, sy * cz, cx * cy * sz));
+  return lap > 0.0f ? inv_nvox / (64.0f * lap) : 0.0f;
+}
+
 // ---------------------------------------------------------------- pass Z + operator
-__global__ void __launch_bounds__(256) k_fft_z_op(double2* __restrict__ spec, int n1, int n2, int nkx, int tx,
-                                                  PlanDev pl, const double2* __restrict__ tw, OpTables T,
+template <typename R>
+__global__ void __launch_bounds__(256) k_fft_z_op(V2<R>* __restrict__ spec, int n1, int n2, int nkx, int tx,
+                                                  PlanDev pl, const V2<R>* __restrict__ tw, OpTables T,
                                                   SpecParams sp, const double* __restrict__ done) {
+  typedef CX<R> cx;
   if (done && *done != 0.0) return;
-  extern __shared__ cplx sm[];
+  extern __shared__ __align__(16) unsigned char smraw[];
   const int cnt = 3 * tx * n2;
-  cplx* a = sm;
-  cplx* b = sm + cnt;
+  cx* a = reinterpret_cast<cx*>(smraw);
+  cx* b = a + cnt;
   const int i = blockIdx.z, ky = blockIdx.y, kx0 = blockIdx.x * tx;
   const size_t zstride = (size_t)n1 * nkx;
   for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
@@ -235,71 +315,35 @@ __global__ void __launch_bounds__(256) k_fft_z_op(double2* __restrict__ spec, in
     const int z = rem / tx, t = rem - z * tx;
     const int kx = kx0 + t;
     const size_t f = 3 * i + c;
-    double2 v = kx < nkx ? spec[(f * n2 + z) * zstride + (size_t)ky * nkx + kx] : make_double2(0.0, 0.0);
-    a[(c * tx + t) * n2 + z] = cmk(v.x, v.y);
+    V2<R> v = kx < nkx ? spec[(f * n2 + z) * zstride + (size_t)ky * nkx + kx] : st2<R>((R)0, (R)0);
+    a[(c * tx + t) * n2 + z] = mk<R>(v.x, v.y);
   }
   __syncthreads();
-  cplx* res = block_fft<-1>(a, b, pl, 3 * tx, tw);
-  cplx* oth = (res == a) ? b : a;
+  cx* res = block_fft<-1, R>(a, b, pl, 3 * tx, tw);
+  cx* oth = (res == a) ? b : a;
+  const float inv_nvox_f = (float)sp.inv_nvox;
   for (int e = threadIdx.x; e < tx * n2; e += blockDim.x) {
     const int t = e / n2, z = e - t * n2;
     const int kx = kx0 + t;
-    cplx X0 = res[(0 * tx + t) * n2 + z], X1 = res[(1 * tx + t) * n2 + z], X2 = res[(2 * tx + t) * n2 + z];
-    cplx Y0, Y1, Y2;
+    cx Y0 = res[(0 * tx + t) * n2 + z], Y1 = res[(1 * tx + t) * n2 + z], Y2 = res[(2 * tx + t) * n2 + z];
     if (kx >= nkx) {
-      Y0 = Y1 = Y2 = cmk(0.0, 0.0);
-    } else if (sp.op == OP_LAPINV) {
-      const double sx = T.s20[kx], sy = T.s21[ky], sz = T.s22[z];
-      const double cx = T.c20[kx], cy = T.c21[ky], cz = T.c22[z];
-      const double lap = fma(sx, cy * cz, fma(cx, sy * cz, cx * cy * sz));
-      const double w = lap > 0.0 ? sp.inv_nvox / (64.0 * lap) : 0.0;
-      Y0 = cscale(X0, w); Y1 = cscale(X1, w); Y2 = cscale(X2, w);
-    } else if (sp.op == OP_PROJECT) {
-      if (kx == 0 && ky == 0 && z == 0) {
-        if (sp.mean_out) {
-          sp.mean_out[3 * i + 0] = X0.x * sp.inv_nvox;
-          sp.mean_out[3 * i + 1] = X1.x * sp.inv_nvox;
-          sp.mean_out[3 * i + 2] = X2.x * sp.inv_nvox;
-        }
-        const double nv = 1.0 / sp.inv_nvox;
-        Y0 = sp.keep[3 * i + 0] ? cmk((X0.x - nv * sp.shift[3 * i + 0]) * sp.inv_nvox, X0.y * sp.inv_nvox) : cmk(0.0, 0.0);
-        Y1 = sp.keep[3 * i + 1] ? cmk((X1.x - nv * sp.shift[3 * i + 1]) * sp.inv_nvox, X1.y * sp.inv_nvox) : cmk(0.0, 0.0);
-        Y2 = sp.keep[3 * i + 2] ? cmk((X2.x - nv * sp.shift[3 * i + 2]) * sp.inv_nvox, X2.y * sp.inv_nvox) : cmk(0.0, 0.0);
-      } else {
-        const int q0 = T.nyq0[kx], q1 = T.nyq1[ky], q2 = T.nyq2[z];
-        double u0, u1, u2;
-        if (q0 + q1 + q2 >= 2) {
-          u0 = u1 = u2 = 0.0;
-        } else if (q0 + q1 + q2 == 1) {
-          u0 = q0; u1 = q1; u2 = q2;
-        } else {
-          const double t0 = T.tan0[kx], t1 = T.tan1[ky], t2 = T.tan2[z];
-          const double inv = rsqrt(fma(t0, t0, fma(t1, t1, t2 * t2)));
-          u0 = t0 * inv; u1 = t1 * inv; u2 = t2 * inv;
-        }
-        // (G X)_ij = u_j sum_l X_il u_l  (scaled by 1/nvox)
-        cplx s = cmk(fma(X0.x, u0, fma(X1.x, u1, X2.x * u2)), fma(X0.y, u0, fma(X1.y, u1, X2.y * u2)));
-        s = cscale(s, sp.inv_nvox);
-        Y0 = cscale(s, u0); Y1 = cscale(s, u1); Y2 = cscale(s, u2);
-      }
-    } else {  // OP_CURL: G_ij = -eps_jkl D_k Fp_il
-      const double2 e0 = T.ph0[kx], e1 = T.ph1[ky], e2 = T.ph2[z];
-      const cplx p0 = cmk(1.0 + e0.x, e0.y), p1 = cmk(1.0 + e1.x, e1.y), p2 = cmk(1.0 + e2.x, e2.y);
-      const cplx m0 = cmk(e0.x - 1.0, e0.y), m1 = cmk(e1.x - 1.0, e1.y), m2 = cmk(e2.x - 1.0, e2.y);
-      const double sc = sp.inv4h * sp.inv_nvox;
-      const cplx D0 = cscale(cmul(m0, cmul(p1, p2)), sc);
-      const cplx D1 = cscale(cmul(p0, cmul(m1, p2)), sc);
-      const cplx D2 = cscale(cmul(p0, cmul(p1, m2)), sc);
-      Y0 = csub(cmul(D2, X1), cmul(D1, X2));
-      Y1 = csub(cmul(D0, X2), cmul(D2, X0));
-      Y2 = csub(cmul(D1, X0), cmul(D0, X1));
+      Y0 = Y1 = Y2 = mk<R>((R)0, (R)0);
+    } else if (sizeof(R) == 4) {
+      // float path: the inverse Laplacian is the only operator it carries
+      const R w = (R)lapinv_weight_f(T, inv_nvox_f, kx, ky, z);
+      Y0 = scl(Y0, w); Y1 = scl(Y1, w); Y2 = scl(Y2, w);
+    } else {
+      cplx X0 = cmk((double)Y0.x, (double)Y0.y), X1 = cmk((double)Y1.x, (double)Y1.y),
+           X2 = cmk((double)Y2.x, (double)Y2.y);
+      apply_op(T, sp, i, kx, ky, z, X0, X1, X2);
+      Y0 = mk<R>((R)X0.x, (R)X0.y); Y1 = mk<R>((R)X1.x, (R)X1.y); Y2 = mk<R>((R)X2.x, (R)X2.y);
     }
     oth[(0 * tx + t) * n2 + z] = Y0;
     oth[(1 * tx + t) * n2 + z] = Y1;
     oth[(2 * tx + t) * n2 + z] = Y2;
   }
   __syncthreads();
-  cplx* res2 = block_fft<+1>(oth, res, pl, 3 * tx, tw);
+  cx* res2 = block_fft<+1, R>(oth, res, pl, 3 * tx, tw);
   for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
     const int c = e / (tx * n2);
     const int rem = e - c * tx * n2;
@@ -307,8 +351,8 @@ __global__ void __launch_bounds__(256) k_fft_z_op(double2* __restrict__ spec, in
     const int kx = kx0 + t;
     if (kx < nkx) {
       const size_t f = 3 * i + c;
-      cplx v = res2[(c * tx + t) * n2 + z];
-      spec[(f * n2 + z) * zstride + (size_t)ky * nkx + kx] = make_double2(v.x, v.y);
+      cx v = res2[(c * tx + t) * n2 + z];
+      spec[(f * n2 + z) * zstride + (size_t)ky * nkx + kx] = st2<R>(v.x, v.y);
     }
   }
 }
@@ -350,6 +394,79 @@ int threads_for(int elems) {
   return t < 64 ? 64 : (t > 256 ? 256 : t);
 }
 
+OpTables op_tables(const rve_s* h) {
+  OpTables T;
+  T.tan0 = h->ax[0].tanh_; T.tan1 = h->ax[1].tanh_; T.tan2 = h->ax[2].tanh_;
+  T.nyq0 = h->ax[0].nyq; T.nyq1 = h->ax[1].nyq; T.nyq2 = h->ax[2].nyq;
+  T.ph0 = h->ax[0].ph; T.ph1 = h->ax[1].ph; T.ph2 = h->ax[2].ph;
+  T.s20 = h->ax[0].s2; T.s21 = h->ax[1].s2; T.s22 = h->ax[2].s2;
+  T.c20 = h->ax[0].c2; T.c21 = h->ax[1].c2; T.c22 = h->ax[2].c2;
+  return T;
+}
+
+template <typename R> const V2<R>* twt(const rve_s* h, int a);
+template <> const double2* twt<double>(const rve_s* h, int a) { return h->ax[a].tw; }
+template <> const float2* twt<float>(const rve_s* h, int a) { return h->ax[a].tw32; }
+template <typename R> V2<R>* spect(const rve_s* h);
+template <> double2* spect<double>(const rve_s* h) { return h->spec; }
+template <> float2* spect<float>(const rve_s* h) { return h->spec32; }
+
+template <typename R>
+cudaError_t fwd(const rve_s* h, const R* in, cudaStream_t s, const double* done, int nf) {
+  const int rpb = rows_per_block(h->n0, h->n1, h->n2, nf);
+  dim3 gx(h->n1 / 2 / rpb, h->n2, nf);
+  size_t shx = 2 * (size_t)rpb * h->n0 * sizeof(CX<R>);
+  {
+    ProfScope ps_(h, RVE_K_FFT_X_R2C, s);
+    k_fft_x_r2c<R><<<gx, threads_for(rpb * h->n0), shx, s>>>(in, spect<R>(h), h->n0, h->n1, h->n2, h->nkx, rpb,
+                                                             to_dev(h->plan[0]), twt<R>(h, 0), done);
+  }
+  const int ty = tile_y(h->n1, h->n2, h->nkx, nf);
+  dim3 gy((h->nkx + ty - 1) / ty, h->n2, nf);
+  size_t shy = 2 * (size_t)ty * h->n1 * sizeof(CX<R>);
+  {
+    ProfScope ps_(h, RVE_K_FFT_Y, s);
+    k_fft_y<-1, R><<<gy, threads_for(ty * h->n1), shy, s>>>(spect<R>(h), h->n1, h->n2, h->nkx, ty,
+                                                            to_dev(h->plan[1]), twt<R>(h, 1), done);
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t zop(const rve_s* h, const SpecParams& sp, cudaStream_t s, const double* done, int nf) {
+  const int tz = tile_z(h->n1, h->n2, h->nkx, nf);
+  dim3 g((h->nkx + tz - 1) / tz, h->n1, nf / 3);
+  size_t sh = 2 * 3 * (size_t)tz * h->n2 * sizeof(CX<R>);
+  const int zthreads = threads_for(3 * tz * h->n2);
+  {
+    ProfScope ps_(h, RVE_K_FFT_Z_OP, s);
+    k_fft_z_op<R><<<g, zthreads, sh, s>>>(spect<R>(h), h->n1, h->n2, h->nkx, tz, to_dev(h->plan[2]), twt<R>(h, 2),
+                                          op_tables(h), sp, done);
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t inv(const rve_s* h, R* out, cudaStream_t s, const double* done, int nf) {
+  const int ty = tile_y(h->n1, h->n2, h->nkx, nf);
+  dim3 gy((h->nkx + ty - 1) / ty, h->n2, nf);
+  size_t shy = 2 * (size_t)ty * h->n1 * sizeof(CX<R>);
+  {
+    ProfScope ps_(h, RVE_K_FFT_Y, s);
+    k_fft_y<+1, R><<<gy, threads_for(ty * h->n1), shy, s>>>(spect<R>(h), h->n1, h->n2, h->nkx, ty,
+                                                            to_dev(h->plan[1]), twt<R>(h, 1), done);
+  }
+  const int rpb = rows_per_block(h->n0, h->n1, h->n2, nf);
+  dim3 gx(h->n1 / 2 / rpb, h->n2, nf);
+  size_t shx = 2 * (size_t)rpb * h->n0 * sizeof(CX<R>);
+  {
+    ProfScope ps_(h, RVE_K_FFT_X_C2R, s);
+    k_fft_x_c2r<R><<<gx, threads_for(rpb * h->n0), shx, s>>>(spect<R>(h), out, h->n0, h->n1, h->n2, h->nkx, rpb,
+                                                             to_dev(h->plan[0]), twt<R>(h, 0), done);
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 void make_plan(int n, FFTPlan* p) {
@@ -363,55 +480,20 @@ void make_plan(int n, FFTPlan* p) {
 }
 
 cudaError_t launch_fft_forward(const rve_s* h, const double* in, cudaStream_t s, const double* done, int nf) {
-  const int rpb = rows_per_block(h->n0, h->n1, h->n2, nf);
-  dim3 gx(h->n1 / 2 / rpb, h->n2, nf);
-  size_t shx = 2 * (size_t)rpb * h->n0 * sizeof(cplx);
-  {
-    ProfScope ps_(h, RVE_K_FFT_X_R2C, s);
-    k_fft_x_r2c<<<gx, threads_for(rpb * h->n0), shx, s>>>(in, h->spec, h->n0, h->n1, h->n2, h->nkx, rpb, to_dev(h->plan[0]), h->ax[0].tw, done);
-  }
-  const int ty = tile_y(h->n1, h->n2, h->nkx, nf);
-  dim3 gy((h->nkx + ty - 1) / ty, h->n2, nf);
-  size_t shy = 2 * (size_t)ty * h->n1 * sizeof(cplx);
-  {
-    ProfScope ps_(h, RVE_K_FFT_Y, s);
-    k_fft_y<-1><<<gy, threads_for(ty * h->n1), shy, s>>>(h->spec, h->n1, h->n2, h->nkx, ty, to_dev(h->plan[1]), h->ax[1].tw, done);
-  }
-  return cudaGetLastError();
+  return fwd<double>(h, in, s, done, nf);
 }
-
 cudaError_t launch_fft_op(const rve_s* h, const SpecParams& sp, cudaStream_t s, const double* done, int nf) {
-  const int tz = tile_z(h->n1, h->n2, h->nkx, nf);
-  dim3 g((h->nkx + tz - 1) / tz, h->n1, nf / 3);
-  size_t sh = 2 * 3 * (size_t)tz * h->n2 * sizeof(cplx);
-  const int zthreads = threads_for(3 * tz * h->n2);
-  OpTables T;
-  T.tan0 = h->ax[0].tanh_; T.tan1 = h->ax[1].tanh_; T.tan2 = h->ax[2].tanh_;
-  T.nyq0 = h->ax[0].nyq; T.nyq1 = h->ax[1].nyq; T.nyq2 = h->ax[2].nyq;
-  T.ph0 = h->ax[0].ph; T.ph1 = h->ax[1].ph; T.ph2 = h->ax[2].ph;
-  T.s20 = h->ax[0].s2; T.s21 = h->ax[1].s2; T.s22 = h->ax[2].s2;
-  T.c20 = h->ax[0].c2; T.c21 = h->ax[1].c2; T.c22 = h->ax[2].c2;
-  {
-    ProfScope ps_(h, RVE_K_FFT_Z_OP, s);
-    k_fft_z_op<<<g, zthreads, sh, s>>>(h->spec, h->n1, h->n2, h->nkx, tz, to_dev(h->plan[2]), h->ax[2].tw, T, sp, done);
-  }
-  return cudaGetLastError();
+  return zop<double>(h, sp, s, done, nf);
 }
-
 cudaError_t launch_fft_inverse(const rve_s* h, double* out, cudaStream_t s, const double* done, int nf) {
-  const int ty = tile_y(h->n1, h->n2, h->nkx, nf);
-  dim3 gy((h->nkx + ty - 1) / ty, h->n2, nf);
-  size_t shy = 2 * (size_t)ty * h->n1 * sizeof(cplx);
-  {
-    ProfScope ps_(h, RVE_K_FFT_Y, s);
-    k_fft_y<+1><<<gy, threads_for(ty * h->n1), shy, s>>>(h->spec, h->n1, h->n2, h->nkx, ty, to_dev(h->plan[1]), h->ax[1].tw, done);
-  }
-  const int rpb = rows_per_block(h->n0, h->n1, h->n2, nf);
-  dim3 gx(h->n1 / 2 / rpb, h->n2, nf);
-  size_t shx = 2 * (size_t)rpb * h->n0 * sizeof(cplx);
-  {
-    ProfScope ps_(h, RVE_K_FFT_X_C2R, s);
-    k_fft_x_c2r<<<gx, threads_for(rpb * h->n0), shx, s>>>(h->spec, out, h->n0, h->n1, h->n2, h->nkx, rpb, to_dev(h->plan[0]), h->ax[0].tw, done);
-  }
-  return cudaGetLastError();
+  return inv<double>(h, out, s, done, nf);
+}
+cudaError_t launch_fft_forward32(const rve_s* h, const float* in, cudaStream_t s, const double* done) {
+  return fwd<float>(h, in, s, done, 3);
+}
+cudaError_t launch_fft_lapinv32(const rve_s* h, const SpecParams& sp, cudaStream_t s, const double* done) {
+  return zop<float>(h, sp, s, done, 3);
+}
+cudaError_t launch_fft_inverse32(const rve_s* h, float* out, cudaStream_t s, const double* done) {
+  return inv<float>(h, out, s, done, 3);
 }

@@ -98,7 +98,20 @@ void carve(rve_s* h, Carver& c) {
   h->t = c.take<double>(9 * nv);
   h->q = c.take<double>(9 * nv);
   h->spec = c.take<double2>(9 * h->nspec);
-  h->partial = c.take<double>(27 * (size_t)RVE_RED_BLOCKS);
+  if (h->opt.precision == 1) {
+    for (int a = 0; a < 3; ++a) h->ax[a].tw32 = c.take<float2>(ns[a]);
+    h->spec32 = c.take<float2>(3 * h->nspec);
+    h->x32 = c.take<float>(9 * nv);
+    h->r32 = c.take<float>(9 * nv);
+    h->p32 = c.take<float>(9 * nv);
+    h->t32 = c.take<float>(9 * nv);
+    h->du32 = c.take<float>(6 * nv);
+  } else {
+    for (int a = 0; a < 3; ++a) h->ax[a].tw32 = nullptr;
+    h->spec32 = nullptr;
+    h->x32 = h->r32 = h->p32 = h->t32 = h->du32 = nullptr;
+  }
+  h->partial = c.take<double>(9 * 4096 + 27 * (size_t)RVE_RED_BLOCKS);
   h->dscal = c.take<double>(64);
   h->dcount = c.take<int32_t>(16);
 }
@@ -313,6 +326,44 @@ rve_status cg_solve(rve_s* h, const uint8_t* mask, double eta, int* iters, bool*
   return RVE_OK;
 }
 
+// Mixed precision: the same CG in FP32 (tangent, vectors, stencils, FFT);
+// the solution is widened to FP64 for the Newton update.  The FP32 loop
+// cannot go below a relative residual of about 1e-6, so eta >= 1e-5.
+rve_status cg_solve32(rve_s* h, const uint8_t* mask, double eta, int* iters, bool* ok) {
+  eta = std::fmax(eta, 1e-5);
+  RVE_CUDA(h, launch_cg_init32(h, eta, h->stream));
+  SpecParams sp = project_params(h, mask, nullptr, nullptr);
+  sp.op = OP_LAPINV;
+  const double* done = h->dscal + DS_DONE;
+  float* d = h->du32;
+  float* u = h->du32 + 3 * h->nvox;
+  int issued = 0;
+  *ok = false;
+  while (issued < h->opt.max_cg) {
+    const int chunk = std::min(CG_CHUNK, h->opt.max_cg - issued);
+    for (int i = 0; i < chunk; ++i) {
+      RVE_CUDA(h, launch_tangent_apply32(h, issued + i == 0, h->stream));
+      RVE_CUDA(h, launch_div32(h, h->t32, d, h->stream));
+      RVE_CUDA(h, launch_fft_forward32(h, d, h->stream, done));
+      RVE_CUDA(h, launch_fft_lapinv32(h, sp, h->stream, done));
+      RVE_CUDA(h, launch_fft_inverse32(h, u, h->stream, done));
+      RVE_CUDA(h, launch_grad_cg32(h, u, mask, h->stream));
+    }
+    issued += chunk;
+    RVE_TRY(read_scalars(h));
+    if (h->hscal[DS_DONE] != 0.0) break;
+  }
+  RVE_CUDA(h, launch_widen_x(h, h->stream));
+  *iters = (int)h->hscal[DS_ITERS];
+  *ok = h->hscal[DS_DONE] != 0.0 && std::isfinite(h->hscal[DS_RR]);
+  // FP32 rounding leaves a small incompatible part in the iterate, which the
+  // projected residual cannot see; one FP64 projection puts the correction
+  // back in the range of G* (compatible fluctuation plus the stress-controlled
+  // mean), so F stays compatible to FP64 round-off
+  RVE_TRY(run_project_stencil(h, h->x, h->x, mask, nullptr));
+  return RVE_OK;
+}
+
 rve_status fail(rve_s* h, rve_status s, const char* msg) {
   h->err = msg;
   return s;
@@ -383,13 +434,14 @@ void Prof::destroy() {
 extern "C" {
 
 size_t rve_workspace_bytes(int n0, int n1, int n2, int n_grains, int precision) {
-  if (precision != 0 || n_grains < 1) return 0;
+  if ((precision != 0 && precision != 1) || n_grains < 1) return 0;
   if (!good_len(n0, 2) || !good_len(n1, 2) || !good_len(n2, 1) || (n0 & 1) || (n1 & 1)) return 0;
   rve_s h;
   h.n0 = n0; h.n1 = n1; h.n2 = n2; h.nkx = n0 / 2 + 1;
   h.nvox = (size_t)n0 * n1 * n2;
   h.nspec = (size_t)h.nkx * n1 * n2;
   h.ngrains = n_grains;
+  h.opt.precision = precision;
   Carver c{nullptr};
   carve(&h, c);
   return c.off;
@@ -507,6 +559,12 @@ rve_status rve_create(const int32_t* grain_id, int n0, int n1, int n2, const dou
             bad(cudaMemcpyAsync((void*)h->ax[a].ph, ph[a].data(), ns[a] * sizeof(double2), cudaMemcpyHostToDevice, s)) ||
             bad(cudaMemcpyAsync((void*)h->ax[a].s2, s2[a].data(), ns[a] * sizeof(double), cudaMemcpyHostToDevice, s)) ||
             bad(cudaMemcpyAsync((void*)h->ax[a].c2, c2[a].data(), ns[a] * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (!fail_ && h->opt.precision == 1) {
+      std::vector<float2> t32(ns[a]);
+      for (int t = 0; t < ns[a]; ++t) t32[t] = make_float2((float)tw[a][t].x, (float)tw[a][t].y);
+      fail_ = bad(cudaMemcpyAsync((void*)h->ax[a].tw32, t32.data(), ns[a] * sizeof(float2), cudaMemcpyHostToDevice, s)) ||
+              bad(cudaStreamSynchronize(s));
+    }
   }
   // initial state: F = Fp = I, S = 0, rho_SSD = rho0 / 12, dF_last = 0
   if (!fail_) {
@@ -554,10 +612,14 @@ rve_status rve_step(rve_t* h, const double dFbar[9], const uint8_t strain_mask[9
     Pb[c] = mask[c] ? 0.0 : Pbar[c];
   }
   auto finish = [&](rve_status st) {
+    const unsigned long long* tot = reinterpret_cast<const unsigned long long*>(h->hcount + 8);
+    loc.local_iters_total = (int64_t)tot[0];
+    loc.local_evals_total = (int64_t)tot[1];
     loc.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (info) *info = loc;
     return st;
   };
+  RVE_CUDA(h, cudaMemsetAsync(h->dcount + 8, 0, 4 * sizeof(int32_t), h->stream));
   rve_status st = run_hardening(h);
   if (st != RVE_OK) return finish(st);
   const int extrap = (h->opt.extrapolate && h->increment > 0) ? 1 : 0;
@@ -589,7 +651,7 @@ rve_status rve_step(rve_t* h, const double dFbar[9], const uint8_t strain_mask[9
     // accurate as the current residual (forcing term min(1e-2, res)); the
     // converged increment does not depend on it
     const double eta = h->opt.cg_adaptive ? std::fmax(h->opt.cg_tol, std::fmin(1e-2, res)) : h->opt.cg_tol;
-    st = cg_solve(h, mask, eta, &ncg, &cgok);
+    st = h->opt.precision == 1 ? cg_solve32(h, mask, eta, &ncg, &cgok) : cg_solve(h, mask, eta, &ncg, &cgok);
     if (st != RVE_OK) return finish(st);
     if (loc.newton_iters < RVE_MAX_NEWTON_LOG) loc.cg_iters[loc.newton_iters] = ncg;
     loc.cg_iters_total += ncg;
@@ -673,7 +735,15 @@ rve_status rve_get_fields(rve_t* h, uint32_t which, void* dst, size_t bytes, int
     case RVE_FIELD_NYE: src = h->nye; break;
     case RVE_FIELD_TAUC: src = h->tauc; break;
     case RVE_FIELD_DGAM: src = h->dgam[h->cur]; break;
-    case RVE_FIELD_TANGENT: src = h->K[h->cur]; break;
+    case RVE_FIELD_TANGENT:
+      if (h->opt.precision == 1) {   // stored as float: widen into the other evaluation buffer
+        double* tmp = h->K[1 - h->cur];
+        RVE_CUDA(h, launch_widen(h, reinterpret_cast<const float*>(h->K[h->cur]), tmp, 81 * h->nvox, h->stream));
+        src = tmp;
+      } else {
+        src = h->K[h->cur];
+      }
+      break;
     case RVE_FIELD_GRAIN: src = h->grain; break;
     case RVE_FIELD_P_EVAL: src = h->P[h->cur]; break;
     case RVE_FIELD_SIGMA:

@@ -43,6 +43,7 @@ struct AxisTables {
   const double2* ph;    // e^{i xi_k}, exactly -1 at Nyquist
   const double* s2;     // sin^2(xi_k / 2)
   const double* c2;     // cos^2(xi_k / 2)
+  const float2* tw32;   // the twiddles rounded to float (mixed precision)
 };
 
 struct Consts {        // material constants read by the hardening and constitutive kernels
@@ -94,6 +95,9 @@ struct rve_s {
   int cur;
   double *R, *x, *r, *p, *t, *q;
   double2* spec;        // 9 * nspec
+  // mixed precision (precision == 1): FP32 conjugate-gradient state
+  float2* spec32;       // 3 * nspec
+  float *x32, *r32, *p32, *t32, *du32;   // 9, 9, 9, 9, 6 components
   double* partial;      // 4 * RVE_RED_BLOCKS
   double* dscal;        // device scalars (see DS_*)
   int32_t* dcount;      // device counters: [0] local max iters, [1] local failures, [4] last-block ticket
@@ -132,12 +136,17 @@ cudaError_t launch_fft_op(const rve_s* h, const SpecParams& sp, cudaStream_t s, 
 cudaError_t launch_fft_inverse(const rve_s* h, double* out, cudaStream_t s, const double* done = nullptr,
                                int nf = 9);
 void make_plan(int n, FFTPlan* p);
+cudaError_t launch_fft_forward32(const rve_s* h, const float* in, cudaStream_t s, const double* done);
+cudaError_t launch_fft_lapinv32(const rve_s* h, const SpecParams& sp, cudaStream_t s, const double* done);
+cudaError_t launch_fft_inverse32(const rve_s* h, float* out, cudaStream_t s, const double* done);
 
 // ---- stencil.cu: G* = D (D^H D)^-1 D^H with real-space rotated-scheme stencils ----
 cudaError_t launch_div(const rve_s* h, const double* X, double* d, int check_done, cudaStream_t s);
 cudaError_t launch_grad(const rve_s* h, const double* u, double* Y, const uint8_t* mask, const double* shift,
                         cudaStream_t s);
 cudaError_t launch_grad_cg(const rve_s* h, const double* u, const uint8_t* mask, cudaStream_t s);
+cudaError_t launch_div32(const rve_s* h, const float* X, float* d, cudaStream_t s);
+cudaError_t launch_grad_cg32(const rve_s* h, const float* u, const uint8_t* mask, cudaStream_t s);
 
 // ---- constitutive.cu ----
 cudaError_t launch_hardening(const rve_s* h, cudaStream_t s);
@@ -150,6 +159,10 @@ cudaError_t launch_cg_update(const rve_s* h, cudaStream_t s);
 cudaError_t launch_norm2(const rve_s* h, const double* a, int ncomp, cudaStream_t s);
 cudaError_t launch_reduce_final(const rve_s* h, int mode, cudaStream_t s);
 cudaError_t launch_cg_init(const rve_s* h, double eta, cudaStream_t s);
+cudaError_t launch_tangent_apply32(const rve_s* h, int first, cudaStream_t s);
+cudaError_t launch_cg_init32(const rve_s* h, double eta, cudaStream_t s);
+cudaError_t launch_widen_x(const rve_s* h, cudaStream_t s);
+cudaError_t launch_widen(const rve_s* h, const float* a, double* b, size_t n, cudaStream_t s);
 cudaError_t launch_axpy_F(const rve_s* h, double lambda, cudaStream_t s);
 cudaError_t launch_predictor(const rve_s* h, const double* dFb, const double* dFb_prev, double ratio,
                              int extrapolate, cudaStream_t s);

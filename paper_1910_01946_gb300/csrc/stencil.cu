@@ -22,75 +22,99 @@ struct Grid3 {
   unsigned nvox;
 };
 
-__device__ __forceinline__ void coords(const Grid3& g, unsigned v, int& x, int& y, int& z) {
-  const unsigned plane = (unsigned)g.n0 * (unsigned)g.n1;
-  z = (int)(v / plane);
-  const unsigned r = v - (unsigned)z * plane;
-  y = (int)(r / (unsigned)g.n0);
-  x = (int)(r - (unsigned)y * (unsigned)g.n0);
-}
+// Tiled stencils.  A tile is tx x ty voxels of one z plane (128 threads,
+// tx a power of two dividing n0, ty = 128 / tx).  Each thread loads the two
+// planes the stencil needs at its position (and the halo threads at the
+// one-voxel halo), stores the z-pair sum (or difference) of every field in
+// shared memory, and the x/y corner sums then share those partial sums
+// between neighbouring voxels: 3 additions per field and voxel instead of 7.
+// Blocks loop over tiles, so the grid (and the reduction partials) stay bounded.
+constexpr int NT = 128;
+constexpr int SMAX = 196;       // max (ty + 1)(tx + 1) over tx in {2, 4, ..., 32}
+constexpr int MAX_BLOCKS = 4096;
+// k_div reduces nine means per thread at the end (a warp-shuffle tree of five
+// FP64 additions each): its grid is capped at four blocks per SM so that each
+// thread first accumulates several tiles and the reduction is amortised
+constexpr int DIV_BLOCKS = 4 * 152;
 
-// voxel indices of the 8 corners n + sgn * a, a in {0,1}^3 (corner index a0 + 2 a1 + 4 a2)
-__device__ __forceinline__ void corners(const Grid3& g, int x, int y, int z, int sgn, unsigned* m) {
-  int xs = x + sgn, ys = y + sgn, zs = z + sgn;
-  xs = xs < 0 ? xs + g.n0 : (xs >= g.n0 ? xs - g.n0 : xs);
-  ys = ys < 0 ? ys + g.n1 : (ys >= g.n1 ? ys - g.n1 : ys);
-  zs = zs < 0 ? zs + g.n2 : (zs >= g.n2 ? zs - g.n2 : zs);
-  const unsigned r00 = (unsigned)g.n0 * ((unsigned)y + (unsigned)g.n1 * (unsigned)z);
-  const unsigned r10 = (unsigned)g.n0 * ((unsigned)ys + (unsigned)g.n1 * (unsigned)z);
-  const unsigned r01 = (unsigned)g.n0 * ((unsigned)y + (unsigned)g.n1 * (unsigned)zs);
-  const unsigned r11 = (unsigned)g.n0 * ((unsigned)ys + (unsigned)g.n1 * (unsigned)zs);
-  m[0] = r00 + x; m[1] = r00 + xs; m[2] = r10 + x; m[3] = r10 + xs;
-  m[4] = r01 + x; m[5] = r01 + xs; m[6] = r11 + x; m[7] = r11 + xs;
-}
+struct Tiling {
+  int tx, ty, bx, by, ntiles, nblocks;
+};
 
-// (D_0 f, D_1 f, D_2 f) from the 8 corner values, without the 1/(4h) factor
-__device__ __forceinline__ void corner_diffs(const double* c, double* d) {
-  const double p00 = c[0] + c[4], p10 = c[1] + c[5], p01 = c[2] + c[6], p11 = c[3] + c[7];  // pairs along z
-  d[0] = (p10 + p11) - (p00 + p01);
-  d[1] = (p01 + p11) - (p00 + p10);
-  d[2] = ((c[4] - c[0]) + (c[5] - c[1])) + ((c[6] - c[2]) + (c[7] - c[3]));
-}
+__device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
-// d_i = sum_l D_l^T X_il (unscaled); partial sums of the 9 input fields for their means
-__global__ void __launch_bounds__(RVE_RED_THREADS) k_div(Grid3 g, const double* __restrict__ X, double* __restrict__ d,
-                                                         double* __restrict__ ds, double* __restrict__ partial,
-                                                         unsigned int* __restrict__ ticket, int check_done) {
+// d_i = sum_l D_l^T X_il (unscaled); partial sums of the 9 input fields for
+// their means.  V is the field type (double, or float for the mixed-precision
+// conjugate gradients); block and grid sums are accumulated in double.
+template <typename V>
+__global__ void __launch_bounds__(NT) k_div(Grid3 g, Tiling T, const V* __restrict__ X,
+                                           V* __restrict__ d, double* __restrict__ ds,
+                                           double* __restrict__ partial, unsigned int* __restrict__ ticket,
+                                           int check_done) {
+  __shared__ V S[9][SMAX];
   __shared__ double sh[32];
   if (check_done && ds[DS_DONE] != 0.0) return;
-  double mean[9];
+  const int W = T.tx + 1;     // row pitch of the staged tile (with its halo)
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const unsigned plane = (unsigned)g.n0 * g.n1;
+  V mean[9];
 #pragma unroll
-  for (int c = 0; c < 9; ++c) mean[c] = 0.0;
-  for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < g.nvox; v += gridDim.x * blockDim.x) {
-    int x, y, z;
-    coords(g, v, x, y, z);
-    unsigned m[8];
-    corners(g, x, y, z, -1, m);
+  for (int f = 0; f < 9; ++f) mean[f] = (V)0;
+  for (int t = blockIdx.x; t < T.ntiles; t += gridDim.x) {
+    const int bxi = t % T.bx, byi = (t / T.bx) % T.by, z = t / (T.bx * T.by);
+    const int x0 = bxi * T.tx, y0 = byi * T.ty;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool inside = y < g.n1;
+    const int xh = wrapi(x0 - 1, g.n0), yh = wrapi(y0 - 1, g.n1), ym = inside ? y : 0;
+    const int zp = wrapi(z - 1, g.n2);
+    const unsigned rz = (unsigned)z * plane, rzp = (unsigned)zp * plane;
+    const unsigned own = (unsigned)ym * g.n0 + x, hrow = (unsigned)yh * g.n0 + x;
+    const unsigned hcol = (unsigned)ym * g.n0 + xh, hcor = (unsigned)yh * g.n0 + xh;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      double acc = 0.0;
-#pragma unroll
-      for (int l = 0; l < 3; ++l) {
-        const double* f = X + (size_t)(3 * i + l) * g.nvox;
-        double c[8];
-#pragma unroll
-        for (int a = 0; a < 8; ++a) c[a] = __ldg(f + m[a]);
-        mean[3 * i + l] += c[0];
-        // D_l^T at n: corners n - a weighted +1 where a_l = 1, -1 where a_l = 0
-        double dd[3];
-        corner_diffs(c, dd);
-        acc += dd[l];
+    for (int f = 0; f < 9; ++f) {
+      const V* F = X + (size_t)f * g.nvox;
+      const bool diff = (f % 3) == 2;      // the z-derivative field of each row
+      const V a = __ldg(F + rz + own), bm = __ldg(F + rzp + own);
+      S[f][(ty + 1) * W + tx + 1] = diff ? bm - a : a + bm;
+      if (inside) mean[f] += a;
+      if (ty == 0) {
+        const V a2 = __ldg(F + rz + hrow), b2 = __ldg(F + rzp + hrow);
+        S[f][tx + 1] = diff ? b2 - a2 : a2 + b2;
       }
-      d[(size_t)i * g.nvox + v] = acc;
+      if (tx == 0) {
+        const V a3 = __ldg(F + rz + hcol), b3 = __ldg(F + rzp + hcol);
+        S[f][(ty + 1) * W] = diff ? b3 - a3 : a3 + b3;
+        if (ty == 0) {
+          const V a4 = __ldg(F + rz + hcor), b4 = __ldg(F + rzp + hcor);
+          S[f][0] = diff ? b4 - a4 : a4 + b4;
+        }
+      }
     }
+    __syncthreads();
+    if (inside) {
+      const int c11 = (ty + 1) * W + tx + 1;                          // this voxel
+      const int c10 = c11 - 1, c01 = c11 - W, c00 = c11 - W - 1;      // x-1, y-1, both
+      const unsigned v = rz + (unsigned)y * g.n0 + x;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const V* A = S[3 * i];
+        const V* B = S[3 * i + 1];
+        const V* Cz = S[3 * i + 2];
+        const V d0 = (A[c10] + A[c00]) - (A[c11] + A[c01]);
+        const V d1 = (B[c01] + B[c00]) - (B[c11] + B[c10]);
+        const V d2 = (Cz[c11] + Cz[c10]) + (Cz[c01] + Cz[c00]);
+        d[(size_t)i * g.nvox + v] = d0 + d1 + d2;
+      }
+    }
+    __syncthreads();
   }
 #pragma unroll
   for (int c = 0; c < 9; ++c) {
-    const double s = blk_sum(mean[c], sh);
-    if (threadIdx.x == 0) partial[(size_t)c * gridDim.x + blockIdx.x] = s;
+    const double s = blk_sum((double)mean[c], sh);
+    if (tx == 0 && ty == 0) partial[(size_t)c * gridDim.x + blockIdx.x] = s;
   }
   double tot[9];
-  if (last_block_sums(partial, 9, ticket, sh, tot) && threadIdx.x == 0) {
+  if (last_block_sums(partial, 9, ticket, sh, tot) && tx == 0 && ty == 0) {
     for (int c = 0; c < 9; ++c) ds[DS_XMEAN + c] = tot[c] / (double)g.nvox;
   }
 }
@@ -100,87 +124,116 @@ struct ZeroMode {
   int keep[9];
 };
 
-// Y_ij = D_j u_i (unscaled) + keep_ij (mean_ij - shift_ij); partial of sum Y^2 -> ds[DS_NORM]
-__global__ void __launch_bounds__(RVE_RED_THREADS) k_grad(Grid3 g, const double* __restrict__ u, double* __restrict__ Y,
-                                                          ZeroMode zm, double* __restrict__ ds,
-                                                          double* __restrict__ partial, unsigned int* __restrict__ ticket) {
+// Forward gradient of the three potentials, D_j u_i (unscaled), plus the zero
+// mode.  CG = false: Y = q, partial of sum Y^2 -> ds[DS_NORM].  CG = true:
+// x += alpha p, r -= alpha q, rr' = r . r, beta, iteration count, done test.
+template <bool CG, typename V>
+__global__ void __launch_bounds__(NT) k_grad_t(Grid3 g, Tiling T, const V* __restrict__ u, ZeroMode zm,
+                                              double* __restrict__ Y, V* __restrict__ x,
+                                              V* __restrict__ r, const V* __restrict__ p,
+                                              double* __restrict__ ds, double* __restrict__ partial,
+                                              unsigned int* __restrict__ ticket) {
+  __shared__ V SP[3][SMAX], SM[3][SMAX];
   __shared__ double sh[32];
-  double off[9];
+  if (CG && ds[DS_DONE] != 0.0) return;
+  const V alpha = CG ? (V)ds[DS_ALPHA] : (V)0;
+  V off[9];
 #pragma unroll
-  for (int c = 0; c < 9; ++c) off[c] = zm.keep[c] ? ds[DS_XMEAN + c] + zm.add[c] : 0.0;
-  double acc = 0.0;
-  for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < g.nvox; v += gridDim.x * blockDim.x) {
-    int x, y, z;
-    coords(g, v, x, y, z);
-    unsigned m[8];
-    corners(g, x, y, z, +1, m);
+  for (int c = 0; c < 9; ++c) off[c] = zm.keep[c] ? (V)(ds[DS_XMEAN + c] + zm.add[c]) : (V)0;
+  const int W = T.tx + 1;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const unsigned plane = (unsigned)g.n0 * g.n1;
+  V acc = (V)0;
+  for (int t = blockIdx.x; t < T.ntiles; t += gridDim.x) {
+    const int bxi = t % T.bx, byi = (t / T.bx) % T.by, z = t / (T.bx * T.by);
+    const int x0 = bxi * T.tx, y0 = byi * T.ty;
+    const int xi = x0 + tx, yi = y0 + ty;
+    const bool inside = yi < g.n1;
+    // high halo: row y0 + ty and column x0 + tx.  When n1 cuts the tile, the
+    // +1 neighbour of the last inside row is the first outside thread row,
+    // whose threads load row wrap(n1) = 0 (ym), so the halo row is not used.
+    const int xh = wrapi(x0 + T.tx, g.n0), yh = (y0 + T.ty) % g.n1, ym = inside ? yi : 0;
+    const int zn = wrapi(z + 1, g.n2);
+    const unsigned rz = (unsigned)z * plane, rzn = (unsigned)zn * plane;
+    const unsigned own = (unsigned)ym * g.n0 + xi, hrow = (unsigned)yh * g.n0 + xi;
+    const unsigned hcol = (unsigned)ym * g.n0 + xh, hcor = (unsigned)yh * g.n0 + xh;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      const double* f = u + (size_t)i * g.nvox;
-      double c[8], d[3];
-#pragma unroll
-      for (int a = 0; a < 8; ++a) c[a] = __ldg(f + m[a]);
-      corner_diffs(c, d);
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const double yv = d[j] + off[3 * i + j];
-        Y[(size_t)(3 * i + j) * g.nvox + v] = yv;
-        acc = fma(yv, yv, acc);
+      const V* F = u + (size_t)i * g.nvox;
+      const V a = __ldg(F + rz + own), c = __ldg(F + rzn + own);
+      SP[i][ty * W + tx] = a + c;
+      SM[i][ty * W + tx] = c - a;
+      if (ty == T.ty - 1) {
+        const V a2 = __ldg(F + rz + hrow), c2 = __ldg(F + rzn + hrow);
+        SP[i][T.ty * W + tx] = a2 + c2;
+        SM[i][T.ty * W + tx] = c2 - a2;
+      }
+      if (tx == T.tx - 1) {
+        const V a3 = __ldg(F + rz + hcol), c3 = __ldg(F + rzn + hcol);
+        SP[i][ty * W + T.tx] = a3 + c3;
+        SM[i][ty * W + T.tx] = c3 - a3;
+        if (ty == T.ty - 1) {
+          const V a4 = __ldg(F + rz + hcor), c4 = __ldg(F + rzn + hcor);
+          SP[i][T.ty * W + T.tx] = a4 + c4;
+          SM[i][T.ty * W + T.tx] = c4 - a4;
+        }
       }
     }
+    __syncthreads();
+    if (inside) {
+      const unsigned v = rz + (unsigned)yi * g.n0 + xi;
+      const int c00 = ty * W + tx, c10 = c00 + 1, c01 = c00 + W, c11 = c00 + W + 1;   // +x, +y, both
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const V* Pp = SP[i];
+        const V* Mm = SM[i];
+        const V q0 = (Pp[c10] + Pp[c11]) - (Pp[c00] + Pp[c01]);
+        const V q1 = (Pp[c01] + Pp[c11]) - (Pp[c00] + Pp[c10]);
+        const V q2 = (Mm[c00] + Mm[c10]) + (Mm[c01] + Mm[c11]);
+        const V qv[3] = {q0 + off[3 * i], q1 + off[3 * i + 1], q2 + off[3 * i + 2]};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const size_t e = (size_t)(3 * i + j) * g.nvox + v;
+          if (CG) {
+            x[e] = fma(alpha, p[e], x[e]);
+            const V rv = fma(-alpha, qv[j], r[e]);
+            r[e] = rv;
+            acc = fma(rv, rv, acc);
+          } else {
+            Y[e] = (double)qv[j];
+            acc = fma(qv[j], qv[j], acc);
+          }
+        }
+      }
+    }
+    __syncthreads();
   }
-  const double s = blk_sum(acc, sh);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  const double s = blk_sum((double)acc, sh);
+  if (tx == 0 && ty == 0) partial[blockIdx.x] = s;
   double tot;
-  if (last_block_sums(partial, 1, ticket, sh, &tot) && threadIdx.x == 0) ds[DS_NORM] = tot;
+  if (last_block_sums(partial, 1, ticket, sh, &tot) && tx == 0 && ty == 0) {
+    if (CG) {
+      ds[DS_BETA] = tot / ds[DS_RR];
+      ds[DS_RR] = tot;
+      ds[DS_ITERS] += 1.0;
+      if (!(tot > ds[DS_STOP])) ds[DS_DONE] = 1.0;
+    } else {
+      ds[DS_NORM] = tot;
+    }
+  }
 }
 
-// CG step fused with the gradient: q_ij = D_j u_i + keep_ij mean(t_ij);
-// x += alpha p; r -= alpha q; rr' = r . r; beta = rr'/rr; iteration count; done test.
-__global__ void __launch_bounds__(RVE_RED_THREADS) k_grad_cg(Grid3 g, const double* __restrict__ u, ZeroMode zm,
-                                                             double* __restrict__ x, double* __restrict__ r,
-                                                             const double* __restrict__ p, double* __restrict__ ds,
-                                                             double* __restrict__ partial,
-                                                             unsigned int* __restrict__ ticket) {
-  __shared__ double sh[32];
-  if (ds[DS_DONE] != 0.0) return;
-  const double alpha = ds[DS_ALPHA];
-  double off[9];
-#pragma unroll
-  for (int c = 0; c < 9; ++c) off[c] = zm.keep[c] ? ds[DS_XMEAN + c] : 0.0;
-  double acc = 0.0;
-  for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < g.nvox; v += gridDim.x * blockDim.x) {
-    int xx, yy, zz;
-    coords(g, v, xx, yy, zz);
-    unsigned m[8];
-    corners(g, xx, yy, zz, +1, m);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const double* f = u + (size_t)i * g.nvox;
-      double c[8], d[3];
-#pragma unroll
-      for (int a = 0; a < 8; ++a) c[a] = __ldg(f + m[a]);
-      corner_diffs(c, d);
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const size_t e = (size_t)(3 * i + j) * g.nvox + v;
-        const double q = d[j] + off[3 * i + j];
-        x[e] = fma(alpha, p[e], x[e]);
-        const double rv = fma(-alpha, q, r[e]);
-        r[e] = rv;
-        acc = fma(rv, rv, acc);
-      }
-    }
-  }
-  const double s = blk_sum(acc, sh);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s;
-  double tot;
-  if (last_block_sums(partial, 1, ticket, sh, &tot) && threadIdx.x == 0) {
-    ds[DS_BETA] = tot / ds[DS_RR];
-    ds[DS_RR] = tot;
-    ds[DS_ITERS] += 1.0;
-    if (!(tot > ds[DS_STOP])) ds[DS_DONE] = 1.0;
-  }
+Tiling tiling_of(const rve_s* h) {
+  Tiling T;
+  int tx = 1;
+  while (tx * 2 <= 32 && h->n0 % (tx * 2) == 0) tx *= 2;
+  T.tx = tx;
+  T.ty = NT / tx;
+  T.bx = h->n0 / tx;
+  T.by = (h->n1 + T.ty - 1) / T.ty;
+  T.ntiles = T.bx * T.by * h->n2;
+  T.nblocks = T.ntiles < MAX_BLOCKS ? T.ntiles : MAX_BLOCKS;
+  return T;
 }
 
 Grid3 grid_of(const rve_s* h) {
@@ -202,29 +255,57 @@ ZeroMode zero_mode(const uint8_t* mask, const double* shift) {
 }  // namespace
 
 cudaError_t launch_div(const rve_s* h, const double* X, double* d, int check_done, cudaStream_t s) {
+  Tiling T = tiling_of(h);
+  if (T.nblocks > DIV_BLOCKS) T.nblocks = DIV_BLOCKS;
   {
     ProfScope ps_(h, RVE_K_STENCIL, s);
-    k_div<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(grid_of(h), X, d, h->dscal, h->partial,
-                                                     (unsigned int*)(h->dcount + 4), check_done);
+    k_div<double><<<T.nblocks, dim3(T.tx, T.ty), 0, s>>>(grid_of(h), T, X, d, h->dscal, h->partial,
+                                                         (unsigned int*)(h->dcount + 4), check_done);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_grad(const rve_s* h, const double* u, double* Y, const uint8_t* mask, const double* shift,
                         cudaStream_t s) {
+  const Tiling T = tiling_of(h);
   {
     ProfScope ps_(h, RVE_K_STENCIL, s);
-    k_grad<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(grid_of(h), u, Y, zero_mode(mask, shift), h->dscal,
-                                                      h->partial, (unsigned int*)(h->dcount + 4));
+    k_grad_t<false, double><<<T.nblocks, dim3(T.tx, T.ty), 0, s>>>(grid_of(h), T, u, zero_mode(mask, shift), Y,
+                                                                   nullptr, nullptr, nullptr, h->dscal, h->partial,
+                                                                   (unsigned int*)(h->dcount + 4));
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_grad_cg(const rve_s* h, const double* u, const uint8_t* mask, cudaStream_t s) {
+  const Tiling T = tiling_of(h);
   {
     ProfScope ps_(h, RVE_K_CG_UPDATE, s);
-    k_grad_cg<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(grid_of(h), u, zero_mode(mask, nullptr), h->x, h->r, h->p,
-                                                         h->dscal, h->partial, (unsigned int*)(h->dcount + 4));
+    k_grad_t<true, double><<<T.nblocks, dim3(T.tx, T.ty), 0, s>>>(grid_of(h), T, u, zero_mode(mask, nullptr),
+                                                                  nullptr, h->x, h->r, h->p, h->dscal, h->partial,
+                                                                  (unsigned int*)(h->dcount + 4));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_div32(const rve_s* h, const float* X, float* d, cudaStream_t s) {
+  Tiling T = tiling_of(h);
+  if (T.nblocks > DIV_BLOCKS) T.nblocks = DIV_BLOCKS;
+  {
+    ProfScope ps_(h, RVE_K_STENCIL, s);
+    k_div<float><<<T.nblocks, dim3(T.tx, T.ty), 0, s>>>(grid_of(h), T, X, d, h->dscal, h->partial,
+                                                        (unsigned int*)(h->dcount + 4), 1);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_cg32(const rve_s* h, const float* u, const uint8_t* mask, cudaStream_t s) {
+  const Tiling T = tiling_of(h);
+  {
+    ProfScope ps_(h, RVE_K_CG_UPDATE, s);
+    k_grad_t<true, float><<<T.nblocks, dim3(T.tx, T.ty), 0, s>>>(grid_of(h), T, u, zero_mode(mask, nullptr), nullptr,
+                                                                 h->x32, h->r32, h->p32, h->dscal, h->partial,
+                                                                 (unsigned int*)(h->dcount + 4));
   }
   return cudaGetLastError();
 }

@@ -111,6 +111,72 @@ __global__ void __launch_bounds__(RVE_RED_THREADS) k_cg_update(size_t n, double*
   }
 }
 
+// Mixed precision: the same CG step with FP32 tangent and vectors (block and
+// grid sums in FP64).  p = r (first) or r + beta p; t = K : p; alpha = rr / p.t
+__global__ void __launch_bounds__(RVE_RED_THREADS) k_tangent_apply32(size_t nvox, const float* __restrict__ K,
+                                                                     const float* __restrict__ r, float* __restrict__ p,
+                                                                     float* __restrict__ t, double* __restrict__ ds,
+                                                                     int first, double* __restrict__ partial,
+                                                                     unsigned int* __restrict__ ticket) {
+  __shared__ double sh[32];
+  if (ds[DS_DONE] != 0.0) return;
+  const float beta = first ? 0.0f : (float)ds[DS_BETA];
+  float acc = 0.0f;
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (size_t)gridDim.x * blockDim.x) {
+    float pv[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float rv = r[k * nvox + v];
+      pv[k] = first ? rv : fmaf(beta, p[k * nvox + v], rv);
+      p[k * nvox + v] = pv[k];
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      float sacc = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 9; ++j) sacc = fmaf(__ldcs(K + (size_t)(9 * i + j) * nvox + v), pv[j], sacc);
+      t[i * nvox + v] = sacc;
+      acc = fmaf(pv[i], sacc, acc);
+    }
+  }
+  const double s = block_sum((double)acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  const double tot = last_block_sum(partial, ticket, sh);
+  if (threadIdx.x == 0 && !isnan(tot)) {
+    ds[DS_PKP] = tot;
+    ds[DS_ALPHA] = ds[DS_RR] / tot;
+  }
+}
+
+// x32 = 0; r32 = -R (rounded); rr; stop = eta^2 rr; iteration count 0
+__global__ void __launch_bounds__(RVE_RED_THREADS) k_cg_init32(size_t n, float* __restrict__ x, float* __restrict__ r,
+                                                               const double* __restrict__ R, double* __restrict__ ds,
+                                                               double eta, double* __restrict__ partial,
+                                                               unsigned int* __restrict__ ticket) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    x[e] = 0.0f;
+    const float rv = (float)(-R[e]);
+    r[e] = rv;
+    acc += (double)rv * (double)rv;
+  }
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  const double tot = last_block_sum(partial, ticket, sh);
+  if (threadIdx.x == 0 && !isnan(tot)) {
+    ds[DS_RR] = tot;
+    ds[DS_STOP] = eta * eta * tot;
+    ds[DS_ITERS] = 0.0;
+    ds[DS_DONE] = (tot > 0.0) ? 0.0 : 1.0;
+  }
+}
+
+__global__ void k_widen(size_t n, const float* __restrict__ a, double* __restrict__ b) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    b[e] = (double)a[e];
+}
+
 // x = 0; r = -R; rr = r . r; stop = eta^2 rr; iteration count 0
 __global__ void __launch_bounds__(RVE_RED_THREADS) k_cg_init(size_t n, double* __restrict__ x, double* __restrict__ r,
                                                              const double* __restrict__ R, double* __restrict__ ds,
@@ -405,6 +471,41 @@ cudaError_t launch_output_field(const rve_s* h, int which, const double* P, cons
   {
     ProfScope ps_(h, RVE_K_OTHER, s);
     k_output<<<grid_for(h->nvox, 128), 128, 0, s>>>(h->nvox, which, h->grain, h->grainR, P, h->F_c, S, dst);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tangent_apply32(const rve_s* h, int first, cudaStream_t s) {
+  {
+    ProfScope ps_(h, RVE_K_TANGENT_APPLY, s);
+    k_tangent_apply32<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, reinterpret_cast<const float*>(h->K[h->cur]),
+                                                                 h->r32, h->p32, h->t32, h->dscal, first, h->partial,
+                                                                 (unsigned int*)(h->dcount + 4));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_init32(const rve_s* h, double eta, cudaStream_t s) {
+  {
+    ProfScope ps_(h, RVE_K_OTHER, s);
+    k_cg_init32<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(9 * h->nvox, h->x32, h->r32, h->R, h->dscal, eta,
+                                                           h->partial, (unsigned int*)(h->dcount + 4));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_widen_x(const rve_s* h, cudaStream_t s) {
+  {
+    ProfScope ps_(h, RVE_K_OTHER, s);
+    k_widen<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(9 * h->nvox, h->x32, h->x);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_widen(const rve_s* h, const float* a, double* b, size_t n, cudaStream_t s) {
+  {
+    ProfScope ps_(h, RVE_K_OTHER, s);
+    k_widen<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(n, a, b);
   }
   return cudaGetLastError();
 }

@@ -49,4 +49,4 @@ def test_struct_layouts_match_header():
     import paper_1910_01946_gb300 as pkg
     assert C.sizeof(pkg.rve_options) == 4 * 8 + 8 * 4
     assert C.sizeof(pkg.rve_material) == 7 * 8 + 6 * 8 + 8 + 5 * 8 + 8
-    assert pkg.rve_step_info.residual.offset == 24
+    assert pkg.rve_step_info.local_iters_total.offset == 24 and pkg.rve_step_info.residual.offset == 40

@@ -223,3 +223,31 @@ def test_full_size_workload_sampled(pkg):
         assert relerr(Pe[sel], r.P) < 1e-10
         assert relerr(Ke[sel], r.K) < 1e-9
     g.close()
+
+
+@pytest.mark.parametrize("wl", [rvegen.Workload("cu8", 8, 5, "Cu", 0.004, 4, seed=31)], ids=["cu8x4"])
+def test_mixed_precision_increments_match_oracle(pkg, wl):
+    """precision = 1: FP32 conjugate gradients, FP64 local update and residual.
+    Newton converges the FP64 residual, so the increment is the FP64 one."""
+    g, o, curve = run_both(pkg, wl, wl.increments, gpu_opts=dict(precision=1))
+    shape = g.shape
+    for name, ref in (("F", to_field(o.F, shape)), ("P", to_field(o.P, shape)), ("FP", to_field(o.Fp, shape))):
+        assert relerr(g.field(name), ref) < 1e-9, name
+    assert relerr(g.field("RHO_SSD"), o.rho_ssd.reshape(shape + (12,))) < 1e-9
+    assert relerr(g.field("RHO_GND"), o.rho_gnd.reshape(shape + (12,))) < 1e-9
+    assert g.field("TANGENT").dtype == np.float64
+    g.close()
+
+
+def test_mixed_precision_matches_fp64_path_cu16(pkg):
+    wl = rvegen.WORKLOADS["cu16"]
+    gid, quat, mat = wl.inputs()
+    a = pkg.RVE(gid, quat, mat, wl.edge)
+    b = pkg.RVE(gid, quat, mat, wl.edge, precision=1)
+    for k in range(4):
+        ia = a.step(wl.dFbar(), MASK, np.zeros(9), wl.dt)
+        ib = b.step(wl.dFbar(), MASK, np.zeros(9), wl.dt)
+    for name in ("F", "P", "FP", "RHO_GND", "SIGMA"):
+        assert relerr(b.field(name), a.field(name)) < 1e-9, name
+    assert relerr(b.macro_stress()[0], a.macro_stress()[0]) < 1e-9
+    a.close(); b.close()
