@@ -106,12 +106,16 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- roofline
-# FP64 operations of the local update, counted from the kernel's arithmetic
-# (an FMA counts 2; constant Schmid-tensor entries 0 and +-1 folded): per voxel
-# set-up (frame rotation, trial elastic state), per residual evaluation, per
-# Newton iteration (Jacobian, LU, solve) and per voxel for the tangent.
-CONST_SETUP, CONST_EVAL, CONST_ITER, CONST_TANGENT = 180.0, 500.0, 1530.0, 8760.0
-CONST_BYTES = 364 + 864        # reads F, dF, Fp^-1, tauc, S, grain; writes P, K, S, dgam
+# FP64 operations of the local update, counted from the kernels' arithmetic
+# (an FMA counts 2; constant Schmid-tensor entries 0 and +-1 folded).  k_local:
+# per voxel set-up (frame rotation, trial elastic state), per residual
+# evaluation, per Newton iteration (Jacobian, LU, solve).  k_tangent: per
+# voxel set-up, one evaluation, Jacobian and LU, P, and the nine directions
+# of dP/dF.
+CONST_SETUP, CONST_EVAL, CONST_ITER = 180.0, 500.0, 1532.0
+TANGENT_FLOPS = 180.0 + 500.0 + 1320.0 + 146.0 + 180.0 + 135.0 + 9 * 780.0
+CONST_BYTES = 364 + 144        # reads F, dF, Fp^-1, tauc, S, grain; writes S, dgam
+TANGENT_BYTES = 364 + 720      # reads F, dF, Fp^-1, tauc, S, grain; writes P, K
 
 
 def kernel_models(n0, n1, n2, local=None):
@@ -132,11 +136,14 @@ def kernel_models(n0, n1, n2, local=None):
         "fft_z_op": (fz, 2 * 9 * nspec * 16),
         "fft_x_c2r": (fx, 9 * nvox * 8 + 9 * nspec * 16),
         "tangent_apply": (nvox * (162 + 18 + 18), nvox * (81 + 9 + 9 + 9 + 9) * 8),
-        # divergence stencil 9 -> 3 fields: 3 corner differences per field + row sums + means
-        "stencil": (nvox * (9 * 7 + 6 + 9), nvox * (9 + 3) * 8),
-        # gradient stencil 3 -> 9 fused with x += alpha p, r -= alpha q, r.r
-        "cg_update": (nvox * (3 * 17 + 9 + 27 * 2), nvox * (3 + 9 * 5) * 8),
-    } | ({"constitutive": ((local[0] * nvox * (CONST_SETUP + CONST_TANGENT) + local[1] * CONST_ITER
+        # tiled divergence 9 -> 3 fields: per field a z-pair sum and 3 corner-sum
+        # additions, 2 row additions per row, 9 means
+        "stencil": (nvox * (9 * 4 + 6 + 9), nvox * (9 + 3) * 8),
+        # tiled gradient 3 -> 9 (z-pair sum and difference, 3 x 3 corner sums),
+        # zero-mode offsets, fused x += alpha p, r -= alpha q, r . r (27 FMA)
+        "cg_update": (nvox * (6 + 27 + 9 + 27 * 2), nvox * (3 + 9 * 5) * 8),
+        "tangent_build": (nvox * TANGENT_FLOPS, nvox * TANGENT_BYTES),
+    } | ({"constitutive": ((local[0] * nvox * CONST_SETUP + local[1] * CONST_ITER
                             + local[2] * CONST_EVAL) / local[0], nvox * CONST_BYTES)}
          if local and local[0] else {})
 
@@ -215,6 +222,21 @@ def oracle_sample(wl, frac=0.08, n_cg=2, seed=0):
     per_inc = REF_EVALS_PER_INC * nv * t_eval + REF_CG_PER_INC * t_cg + t_hard
     sample_s = t_hard + t_eval * len(idx) + t_cg * n_cg
     return per_inc, sample_s, len(idx), t_eval, t_cg
+
+
+def reduce_over_ranks(ms, units, device="cpu"):
+    """Replicas: the job's time is the slowest rank's, its work the sum of all
+    ranks' (weak scaling, no data exchange between ranks).  Returns
+    (max ms, total units); a single process returns its own values."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), float(units)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
 
 
 def cpu_cores():
@@ -316,13 +338,8 @@ def main():
     stats = rve.kernel_stats()
     rve.profile(False)
     evals = stats["constitutive"][0]
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    cg_t = torch.tensor([cg_total], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(cg_t, op=dist.ReduceOp.SUM)
-    ms_max = float(ms_t.item())
-    value = nvox * float(cg_t.item()) / (ms_max / 1e3)
+    ms_max, cg_all = reduce_over_ranks(ms, cg_total, device=dev)
+    value = nvox * cg_all / (ms_max / 1e3)
     P_macro, sig_macro = rve.macro_stress()
     launches = int(sum(v[0] for v in stats.values()))
     rve.close()
@@ -357,14 +374,10 @@ def main():
             cg2 += e2e_step()["cg_iters_total"]
         barrier()
         el = time.perf_counter() - t0
-        el_t = torch.tensor([el], dtype=torch.float64, device=dev)
-        cg2_t = torch.tensor([cg2], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(el_t, op=dist.ReduceOp.MAX)
-            dist.all_reduce(cg2_t, op=dist.ReduceOp.SUM)
-        e2e = {"value": nvox * float(cg2_t.item()) / float(el_t.item()), "unit": "voxel-iter/s",
+        el_max, cg2_all = reduce_over_ranks(el, cg2, device=dev)
+        e2e = {"value": nvox * cg2_all / el_max, "unit": "voxel-iter/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "ms_per_step": 1e3 * float(el_t.item()) / a.steps,
+               "ms_per_step": 1e3 * el_max / a.steps,
                "path": "rve_step with host load arrays + rve_get_fields(SIGMA, RHO_GND) to pinned host + macro stress"}
         r2.close()
 

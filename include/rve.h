@@ -204,7 +204,7 @@ rve_status rve_restore(rve_t* rve, const void* host_buf, size_t bytes);
 enum {
   RVE_K_FFT_X_R2C = 0, RVE_K_FFT_Y = 1, RVE_K_FFT_Z_OP = 2, RVE_K_FFT_X_C2R = 3,
   RVE_K_CONSTITUTIVE = 4, RVE_K_HARDENING = 5, RVE_K_TANGENT_APPLY = 6, RVE_K_CG_UPDATE = 7,
-  RVE_K_REDUCE = 8, RVE_K_OTHER = 9, RVE_K_STENCIL = 10, RVE_K_COUNT = 11
+  RVE_K_REDUCE = 8, RVE_K_OTHER = 9, RVE_K_STENCIL = 10, RVE_K_TANGENT_BUILD = 11, RVE_K_COUNT = 12
 };
 rve_status rve_profile(rve_t* rve, int enable);
 rve_status rve_kernel_stats(rve_t* rve, int64_t* launches, double* ms);

@@ -270,34 +270,51 @@ __global__ void __launch_bounds__(128) k_hardening(
   for (int k = 0; k < 9; ++k) Fp0inv[k * nvox + v] = Gt[k];
 }
 
-__global__ void __launch_bounds__(128) k_constitutive(
+// State of one voxel at the start of an evaluation: rotation, F~ = R^T F R
+// (F with the line-search step applied), the crystal-frame Fp_prev^-1, the
+// trial elastic right Cauchy-Green tensor A = (F~ Fp_prev^-1)^T (F~ Fp_prev^-1)
+// and the frozen critical resolved shear stresses.
+struct VoxelIn {
+  double R[9], Ft[9], Fpi0[9], A[9], tauc[12];
+};
+
+__device__ __forceinline__ void load_voxel(size_t nvox, size_t v, const int32_t* __restrict__ grain,
+                                           const double* __restrict__ grainR, const double* __restrict__ Fin,
+                                           const double* __restrict__ xdir, double lambda,
+                                           const double* __restrict__ Fp0inv, const double* __restrict__ tauc_g,
+                                           VoxelIn& in) {
+  double Fs[9], T[9], FeTr[9];
+  const int g = grain[v];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) in.R[k] = __ldg(grainR + 9 * g + k);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    double f = Fin[k * nvox + v];
+    if (lambda != 0.0) f = fma(lambda, xdir[k * nvox + v], f);
+    Fs[k] = f;
+    in.Fpi0[k] = Fp0inv[k * nvox + v];
+  }
+  mat3_mul(Fs, in.R, T);
+  mat3_tmul(in.R, T, in.Ft);              // F~ = R^T F R
+  mat3_mul(in.Ft, in.Fpi0, FeTr);
+  mat3_tmul(FeTr, FeTr, in.A);
+#pragma unroll
+  for (int a = 0; a < 12; ++a) in.tauc[a] = tauc_g[a * nvox + v];
+}
+
+// Local Newton on S (data-dependent iteration counts): writes S and dgam.
+__global__ void __launch_bounds__(128) k_local(
     size_t nvox, const int32_t* __restrict__ grain, const double* __restrict__ grainR,
     const double* __restrict__ Fin, const double* __restrict__ xdir, double lambda,
     const double* __restrict__ Fp0inv, const double* __restrict__ tauc_g, const double* __restrict__ Swarm,
-    double* __restrict__ Pout, double* __restrict__ Kout, double* __restrict__ Sout, double* __restrict__ dgout,
-    int32_t* __restrict__ counters, double dt, Consts c, int k32) {
+    double* __restrict__ Sout, double* __restrict__ dgout, int32_t* __restrict__ counters, double dt, Consts c) {
   const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   int iters = 0, failed = 0, evals = 0;
   if (v < nvox) {
-    double R[9], Fs[9], T[9], Ft[9], Fpi0[9];
-    const int g = grain[v];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) R[k] = __ldg(grainR + 9 * g + k);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      double f = Fin[k * nvox + v];
-      if (lambda != 0.0) f = fma(lambda, xdir[k * nvox + v], f);
-      Fs[k] = f;
-      Fpi0[k] = Fp0inv[k * nvox + v];
-    }
-    mat3_mul(Fs, R, T);
-    mat3_tmul(R, T, Ft);                  // F~ = R^T F R
-    double FeTr[9], A[9];
-    mat3_mul(Ft, Fpi0, FeTr);
-    mat3_tmul(FeTr, FeTr, A);
-    double tauc[12];
-#pragma unroll
-    for (int a = 0; a < 12; ++a) tauc[a] = tauc_g[a * nvox + v];
+    VoxelIn in;
+    load_voxel(nvox, v, grain, grainR, Fin, xdir, lambda, Fp0inv, tauc_g, in);
+    const double* A = in.A;
+    const double* tauc = in.tauc;
     double S[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) S[k] = Swarm[k * nvox + v];
@@ -347,12 +364,50 @@ __global__ void __launch_bounds__(128) k_constitutive(
       conv = e.rn <= c.local_tol_abs;
     }
     failed = conv ? 0 : 1;
-
-    // ---- outputs: S, dgam, P and the consistent tangent
 #pragma unroll
     for (int k = 0; k < 6; ++k) Sout[k * nvox + v] = S[k];
 #pragma unroll
     for (int a = 0; a < 12; ++a) dgout[a * nvox + v] = e.dg[a];
+  }
+  // counters: warp-aggregated
+  const unsigned full = 0xffffffffu;
+  int mx = __reduce_max_sync(full, iters);
+  int nf = __reduce_add_sync(full, failed);
+  unsigned si = __reduce_add_sync(full, (unsigned)iters);
+  unsigned se = __reduce_add_sync(full, (unsigned)evals);
+  if ((threadIdx.x & 31) == 0) {
+    if (mx) atomicMax(&counters[0], mx);
+    if (nf) atomicAdd(&counters[1], nf);
+    // 64-bit totals of local Newton iterations and residual evaluations (work accounting)
+    unsigned long long* tot = reinterpret_cast<unsigned long long*>(counters + 8);
+    atomicAdd(&tot[0], (unsigned long long)si);
+    atomicAdd(&tot[1], (unsigned long long)se);
+  }
+}
+
+
+// P and the consistent tangent at the converged S: the same work for every
+// voxel (no data-dependent iterations), so whole warps stay converged.
+__global__ void __launch_bounds__(128) k_tangent(
+    size_t nvox, const int32_t* __restrict__ grain, const double* __restrict__ grainR,
+    const double* __restrict__ Fin, const double* __restrict__ xdir, double lambda,
+    const double* __restrict__ Fp0inv, const double* __restrict__ tauc_g, const double* __restrict__ Sin,
+    double* __restrict__ Pout, double* __restrict__ Kout, double dt, Consts c, int k32) {
+  const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < nvox) {
+    VoxelIn in;
+    load_voxel(nvox, v, grain, grainR, Fin, xdir, lambda, Fp0inv, tauc_g, in);
+    const double* R = in.R;
+    const double* Ft = in.Ft;
+    const double* Fpi0 = in.Fpi0;
+    const double* tauc = in.tauc;
+    double S[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) S[k] = Sin[k * nvox + v];
+    Eval e;
+    evaluate(c, S, in.A, tauc, dt, e);
+    double J[36], dgp[12];
+    int piv[6];
     jacobian(c, e, tauc, dt, J, dgp);
     lu6(J, piv);
     double Fpinv[9], Fe[9], Sf[9], W[9], Q[9];
@@ -422,20 +477,6 @@ __global__ void __launch_bounds__(128) k_constitutive(
       }
     }
   }
-  // counters: warp-aggregated
-  const unsigned full = 0xffffffffu;
-  int mx = __reduce_max_sync(full, iters);
-  int nf = __reduce_add_sync(full, failed);
-  unsigned si = __reduce_add_sync(full, (unsigned)iters);
-  unsigned se = __reduce_add_sync(full, (unsigned)evals);
-  if ((threadIdx.x & 31) == 0) {
-    if (mx) atomicMax(&counters[0], mx);
-    if (nf) atomicAdd(&counters[1], nf);
-    // 64-bit totals of local Newton iterations and residual evaluations (work accounting)
-    unsigned long long* tot = reinterpret_cast<unsigned long long*>(counters + 8);
-    atomicAdd(&tot[0], (unsigned long long)si);
-    atomicAdd(&tot[1], (unsigned long long)se);
-  }
 }
 
 }  // namespace
@@ -456,9 +497,14 @@ cudaError_t launch_constitutive(const rve_s* h, double dt, double lambda, int ou
   const double* warm = warm_buf < 0 ? h->S_c : h->S[warm_buf];
   {
     ProfScope ps_(h, RVE_K_CONSTITUTIVE, s);
-    k_constitutive<<<blocks, 128, 0, s>>>(h->nvox, h->grain, h->grainR, h->F, h->x, lambda, h->Fp0inv, h->tauc,
-                                        warm, h->P[out_buf], h->K[out_buf], h->S[out_buf], h->dgam[out_buf],
-                                        h->dcount, dt, h->cst, h->opt.precision == 1);
+    k_local<<<blocks, 128, 0, s>>>(h->nvox, h->grain, h->grainR, h->F, h->x, lambda, h->Fp0inv, h->tauc, warm,
+                                   h->S[out_buf], h->dgam[out_buf], h->dcount, dt, h->cst);
+  }
+  {
+    ProfScope ps_(h, RVE_K_TANGENT_BUILD, s);
+    k_tangent<<<blocks, 128, 0, s>>>(h->nvox, h->grain, h->grainR, h->F, h->x, lambda, h->Fp0inv, h->tauc,
+                                     h->S[out_buf], h->P[out_buf], h->K[out_buf], dt, h->cst,
+                                     h->opt.precision == 1);
   }
   return cudaGetLastError();
 }
