@@ -47,9 +47,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=47)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
+                    help="replay chunks of CG iterations as captured CUDA graphs")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(rvegen.WORKLOADS))
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(rvegen.WORKLOADS) + ["sweep"],
+                    help="sweep: the 16-RVE grain-size sweep stepped together (rve_step_batch)")
     ap.add_argument("--precision", default="f64", choices=["f64", "mixed"],
                     help="mixed: FP32 conjugate gradients with FP64 local update and residual")
     return ap.parse_args()
@@ -108,14 +111,15 @@ class ClockSampler:
 # ---------------------------------------------------------------- roofline
 # FP64 operations of the local update, counted from the kernels' arithmetic
 # (an FMA counts 2; constant Schmid-tensor entries 0 and +-1 folded).  k_local:
-# per voxel set-up (frame rotation, trial elastic state), per residual
-# evaluation, per Newton iteration (Jacobian, LU, solve).  k_tangent: per
-# voxel set-up, one evaluation, Jacobian and LU, P, and the nine directions
-# of dP/dF.
-CONST_SETUP, CONST_EVAL, CONST_ITER = 180.0, 500.0, 1532.0
-TANGENT_FLOPS = 180.0 + 500.0 + 1320.0 + 146.0 + 180.0 + 135.0 + 9 * 780.0
-CONST_BYTES = 364 + 144        # reads F, dF, Fp^-1, tauc, S, grain; writes S, dgam
-TANGENT_BYTES = 364 + 720      # reads F, dF, Fp^-1, tauc, S, grain; writes P, K
+# per voxel set-up (frame rotation, trial elastic state) and P at the
+# converged S (six 3x3 products), per residual evaluation, per Newton
+# iteration (Jacobian, LU, solve).  k_tangent: per voxel set-up, one
+# evaluation, Jacobian and LU, the intermediate products, and the nine
+# directions of dP/dF.
+CONST_SETUP, CONST_EVAL, CONST_ITER = 180.0 + 270.0, 500.0, 1532.0
+TANGENT_FLOPS = 180.0 + 500.0 + 1320.0 + 146.0 + 180.0 + 9 * 780.0
+CONST_BYTES = 364 + 216        # reads F, dF, Fp^-1, tauc, S, grain; writes S, dgam, P
+TANGENT_BYTES = 364 + 648      # reads F, dF, Fp^-1, tauc, S, grain; writes K
 
 
 def kernel_models(n0, n1, n2, local=None):
@@ -137,8 +141,9 @@ def kernel_models(n0, n1, n2, local=None):
         "fft_x_c2r": (fx, 9 * nvox * 8 + 9 * nspec * 16),
         "tangent_apply": (nvox * (162 + 18 + 18), nvox * (81 + 9 + 9 + 9 + 9) * 8),
         # tiled divergence 9 -> 3 fields: per field a z-pair sum and 3 corner-sum
-        # additions, 2 row additions per row, 9 means
-        "stencil": (nvox * (9 * 4 + 6 + 9), nvox * (9 + 3) * 8),
+        # additions, 2 row additions per row, and the means of the stress-
+        # controlled components (5 under uniaxial tension)
+        "stencil": (nvox * (9 * 4 + 6 + 5), nvox * (9 + 3) * 8),
         # tiled gradient 3 -> 9 (z-pair sum and difference, 3 x 3 corner sums),
         # zero-mode offsets, fused x += alpha p, r -= alpha q, r . r (27 FMA)
         "cg_update": (nvox * (6 + 27 + 9 + 27 * 2), nvox * (3 + 9 * 5) * 8),
@@ -247,8 +252,73 @@ def cpu_cores():
 
 
 # ---------------------------------------------------------------- main
+def run_sweep(a):
+    """The batched grain-size sweep: 16 RVEs (32^3 .. 96^3, 8 .. 400 grains,
+    Cu/Al/Ag/Ni) advanced together, each on its own stream.  Throughput is
+    the sum over RVEs of voxels x CG iterations over the wall time of the
+    batched increments (device synchronised on both sides)."""
+    import torch
+    import paper_1910_01946_gb300 as pkg
+    from paper_1910_01946_gb300 import _build
+    _build.build()
+    pkg.load_library()
+    prec = 1 if a.precision == "mixed" else 0
+    wls = rvegen.sweep_workloads()
+    rves = []
+    for w in wls:
+        gid, quat, mat = w.inputs()
+        rves.append(pkg.RVE(gid, quat, mat, w.edge, own_stream=True, precision=prec, graphs=a.graphs))
+    mask = rvegen.UNIAXIAL_X_MASK
+    dF = [w.dFbar() for w in wls]
+    dts = [w.dt for w in wls]
+    for k in range(a.warmup):
+        try:
+            pkg.step_batch(rves, dF, mask, np.zeros(9), dts)
+        except pkg.RVEError as e:
+            print(json.dumps({"metric": "voxel-iterations/s", "error": f"warm-up increment {k}: {e}"}))
+            raise
+    for r in rves:
+        r.profile(True)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    clocks.start()
+    time.sleep(0.3)
+    t0 = time.perf_counter()
+    work, cg = 0.0, 0
+    for k in range(a.steps):
+        try:
+            infos = pkg.step_batch(rves, dF, mask, np.zeros(9), dts)
+        except pkg.RVEError as e:
+            print(json.dumps({"metric": "voxel-iterations/s", "error": f"timed increment {k}: {e}"}))
+            raise
+        for w, i in zip(wls, infos):
+            work += w.n ** 3 * i["cg_iters_total"]
+            cg += i["cg_iters_total"]
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    clocks.stop()
+    launches = sum(sum(v[0] for v in r.kernel_stats().values()) for r in rves)
+    curve = [{"rve": w.name, "grain_um": round(w.edge * 1e6 * (6.0 / (math.pi * w.n_grains)) ** (1 / 3), 2),
+              "sigma11_MPa": float(r.macro_stress()[1][0, 0])} for w, r in zip(wls, rves)]
+    line = {"metric": "voxel-iterations/s", "value": work / el, "unit": "voxel-iter/s", "n_gpus": 1,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * el / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == 0 else "f64 local update and residual, f32 conjugate gradients",
+            "data": "synthetic",
+            "config": {"workload": "grain-size sweep: 16 RVEs, edges {32,48,64,96}^3, 8-400 grains, Cu/Al/Ag/Ni, "
+                                   "2 % tension in 20 increments, L = 100 um, batched (one stream per RVE)",
+                       "voxels": int(sum(w.n ** 3 for w in wls))},
+            "gpu_launches": launches, "clocks": clocks.summary(),
+            "detail": {"cg_iters_per_increment_all_rves": cg / a.steps, "flow_stress": curve}}
+    for r in rves:
+        r.close()
+    print(json.dumps(line))
+
+
 def main():
     a = parse()
+    if a.workload == "sweep":
+        return run_sweep(a)
     wl = rvegen.WORKLOADS[a.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -310,7 +380,9 @@ def main():
 
     # ---- device-resident run (inputs already on the GPU)
     prec = 1 if a.precision == "mixed" else 0
-    rve = pkg.RVE(gid, quat, mat, wl.edge, device=dev, precision=prec)
+    # a stream of the library's own: the CG chunks are replayed as CUDA graphs,
+    # which the legacy default stream cannot capture
+    rve = pkg.RVE(gid, quat, mat, wl.edge, device=dev, precision=prec, own_stream=True, graphs=a.graphs)
     stream = rve.stream
     for _ in range(a.warmup):
         rve.step(wl.dFbar(), mask, Pbar, wl.dt)
@@ -352,7 +424,7 @@ def main():
         sig_h = torch.empty((9, nvox), dtype=torch.float64).pin_memory()
         gnd_h = torch.empty((12, nvox), dtype=torch.float64).pin_memory()
         load_h = torch.empty(9 + 9, dtype=torch.float64).pin_memory().numpy()
-        r2 = pkg.RVE(gid, quat, mat, wl.edge, device=dev, precision=prec)
+        r2 = pkg.RVE(gid, quat, mat, wl.edge, device=dev, precision=prec, own_stream=True, graphs=a.graphs)
         cg2 = 0
         h2d = 9 * 8 + 9 + 9 * 8
         d2h = sig_h.numel() * 8 + gnd_h.numel() * 8 + 2 * 9 * 8
@@ -410,7 +482,8 @@ def main():
             "data": "synthetic", "config": config,
             "e2e": e2e, "gpu_launches": launches, "roofline": roof_line, "cpu_baseline": cpu,
             "clocks": clocks.summary(),
-            "detail": {"voxel_increments_per_s": world * nvox * a.steps / (ms_max / 1e3),
+            "detail": {"cuda_graphs": bool(a.graphs),
+                       "voxel_increments_per_s": world * nvox * a.steps / (ms_max / 1e3),
                        "cg_iters_per_increment": cg_total / a.steps,
                        "newton_iters_per_increment": newton_total / a.steps,
                        "local_evals_per_increment": evals / a.steps,

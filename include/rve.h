@@ -86,6 +86,14 @@ typedef struct {
                             increment is the FP64 one (outer Newton refinement) */
   int32_t cg_adaptive;   /* nonzero: CG relative tolerance max(cg_tol, min(1e-2, current relative
                             residual)) (inexact Newton; the converged increment is the same) */
+  int32_t krylov;        /* linear solver of the Newton step: 0 conjugate gradients (the paper's
+                            solver), and when no step along the CG direction (converged or cut
+                            off at max_cg) lowers the residual, the same Newton iteration solved
+                            again with BiCGStab (the consistent tangent is not symmetric);
+                            1 BiCGStab only; 2 conjugate gradients only */
+  int32_t graphs;        /* nonzero: chunks of 8 CG iterations are captured once into a CUDA graph
+                            and replayed with one launch (needs a stream other than the legacy
+                            default stream; ignored there).  Results are bit-identical. */
 } rve_options;
 
 #define RVE_MAX_NEWTON_LOG 64
@@ -96,6 +104,7 @@ typedef struct {
   int32_t local_max_iters;
   int32_t local_failures;
   int32_t halvings;
+  int32_t bicgstab_solves;                      /* Newton steps solved by BiCGStab */
   int64_t local_iters_total;                    /* local Newton iterations summed over voxels and evaluations */
   int64_t local_evals_total;                    /* local residual evaluations, likewise */
   double residual;                              /* final relative residual */
@@ -118,7 +127,9 @@ typedef struct {
  * Last local evaluation (the converged one after rve_step, or the one made by
  * rve_eval_constitutive):
  *   P_EVAL: 9; S_EVAL: 6; DGAM: 12 (slip increments); TANGENT: 81
- *   (K_ijkl = dP_ij / dF_kl at component 27*i + 9*j + 3*k + l). */
+ *   (K_ijkl = dP_ij / dF_kl at component 27*i + 9*j + 3*k + l).  rve_step does
+ *   not build the tangent of the converged evaluation (no solve needs it); the
+ *   first TANGENT request, or rve_eval_hardening, builds it from that state. */
 enum {
   RVE_FIELD_F = 0, RVE_FIELD_P = 1, RVE_FIELD_FP = 2, RVE_FIELD_S = 3,
   RVE_FIELD_SIGMA = 4, RVE_FIELD_RHO_SSD = 5, RVE_FIELD_RHO_GND = 6,
@@ -157,6 +168,18 @@ rve_status rve_create(const int32_t* grain_id, int n0, int n1, int n2,
  * increment (the call is atomic). */
 rve_status rve_step(rve_t* rve, const double dFbar[9], const uint8_t strain_mask[9],
                     const double Pbar[9], double dt, rve_step_info* info);
+
+/* Batched increments: n independent handles (different sizes, grain counts,
+ * materials) each advance one increment, concurrently.  One host thread per
+ * handle drives that handle's own stream, so the kernels of different RVEs
+ * overlap on the GPU (the batched grain-size sweep).  dFbar, strain_mask and
+ * Pbar hold 9 values per handle, dt one; info and status (nullable) receive
+ * one entry per handle.  Each handle behaves exactly as under rve_step
+ * (atomic on failure).  Handles must be distinct; for overlap they must use
+ * different streams.  Returns RVE_OK if every step succeeded, else the status
+ * of the first handle (in index order) that failed. */
+rve_status rve_step_batch(rve_t* const* rves, int n, const double* dFbar, const uint8_t* strain_mask,
+                          const double* Pbar, const double* dt, rve_step_info* info, rve_status* status);
 
 /* Volume averages of the first Piola-Kirchhoff stress and of the Cauchy
  * stress P F^T / det F over the committed state; host outputs. */

@@ -44,13 +44,14 @@ class rve_options(C.Structure):
     _fields_ = [("L", C.c_double), ("newton_tol", C.c_double), ("cg_tol", C.c_double),
                 ("local_tol", C.c_double), ("max_newton", C.c_int32), ("max_cg", C.c_int32),
                 ("max_local", C.c_int32), ("max_halvings", C.c_int32), ("extrapolate", C.c_int32),
-                ("precision", C.c_int32), ("cg_adaptive", C.c_int32)]
+                ("precision", C.c_int32), ("cg_adaptive", C.c_int32), ("krylov", C.c_int32),
+                ("graphs", C.c_int32)]
 
 
 class rve_step_info(C.Structure):
     _fields_ = [("converged", C.c_int32), ("newton_iters", C.c_int32), ("cg_iters_total", C.c_int32),
                 ("local_max_iters", C.c_int32), ("local_failures", C.c_int32), ("halvings", C.c_int32),
-                ("local_iters_total", C.c_int64), ("local_evals_total", C.c_int64),
+                ("bicgstab_solves", C.c_int32), ("local_iters_total", C.c_int64), ("local_evals_total", C.c_int64),
                 ("residual", C.c_double), ("seconds", C.c_double), ("cg_iters", C.c_int32 * MAX_NEWTON_LOG),
                 ("residuals", C.c_double * (MAX_NEWTON_LOG + 1))]
 
@@ -62,6 +63,8 @@ _SIGS = {
                              C.c_void_p, C.POINTER(C.c_void_p)]),
     "rve_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                            C.POINTER(rve_step_info)]),
+    "rve_step_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_void_p]),
     "rve_get_macro_stress": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "rve_get_fields": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.c_size_t, C.c_int]),
     "rve_set_fields": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.c_size_t, C.c_int]),
@@ -124,6 +127,40 @@ def rve_create(grain_id, n0, n1, n2, quat, n_grains, mat, opt, d_workspace, ws_b
 def rve_step(h, dFbar, mask, Pbar, dt, info=None):
     return load_library().rve_step(h, _ptr(dFbar), _ptr(mask), _ptr(Pbar), dt,
                                    C.byref(info) if info is not None else None)
+
+
+def rve_step_batch(handles, dFbar, mask, Pbar, dt, infos=None, status=None):
+    """handles: sequence of handle pointers; dFbar, Pbar: (n, 9) float64;
+    mask: (n, 9) uint8; dt: (n,) float64; infos: ctypes array of rve_step_info
+    or None; status: (n,) int32 array or None."""
+    n = len(handles)
+    harr = (C.c_void_p * n)(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    return load_library().rve_step_batch(harr, n, _ptr(dFbar), _ptr(mask), _ptr(Pbar), _ptr(dt),
+                                         C.cast(infos, C.c_void_p) if infos is not None else None,
+                                         _ptr(status) if status is not None else None)
+
+
+def step_batch(rves, dFbar, mask, Pbar, dt):
+    """Advance RVE objects by one increment each, concurrently (their own streams).
+    dFbar, Pbar: (n, 9); mask: (9,) or (n, 9); dt: scalar or (n,).  Returns the
+    per-handle step dictionaries; raises on the first failed status."""
+    n = len(rves)
+    dF = np.ascontiguousarray(np.broadcast_to(np.asarray(dFbar, dtype=np.float64).reshape(-1, 9), (n, 9)))
+    Pb = np.ascontiguousarray(np.broadcast_to(np.asarray(Pbar, dtype=np.float64).reshape(-1, 9), (n, 9)))
+    mk = np.ascontiguousarray(np.broadcast_to(np.asarray(mask, dtype=np.uint8).reshape(-1, 9), (n, 9)))
+    dts = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64).reshape(-1), (n,)))
+    infos = (rve_step_info * n)()
+    status = np.zeros(n, dtype=np.int32)
+    rve_step_batch([r.h for r in rves], dF, mk, Pb, dts, infos, status)
+    out = []
+    for i, r in enumerate(rves):
+        inf = infos[i]
+        out.append(dict(status=int(status[i]), converged=bool(inf.converged), newton_iters=inf.newton_iters,
+                        cg_iters_total=inf.cg_iters_total, local_iters_total=inf.local_iters_total,
+                        local_evals_total=inf.local_evals_total, residual=inf.residual, seconds=inf.seconds))
+        if status[i] != RVE_OK:
+            raise RVEError(int(status[i]), f"rve_step_batch[{i}]: {rve_last_error(r.h)}")
+    return out
 
 
 def rve_get_macro_stress(h, P, sig):
@@ -189,7 +226,7 @@ def rve_destroy(h):
 
 # ---- handle wrapper ---------------------------------------------------------
 DEFAULT_OPTIONS = dict(newton_tol=1e-11, cg_tol=1e-11, local_tol=1e-14, max_newton=100, max_cg=2000,
-                       max_local=60, max_halvings=12, extrapolate=1, precision=0, cg_adaptive=1)
+                       max_local=60, max_halvings=12, extrapolate=1, precision=0, cg_adaptive=1, krylov=0, graphs=1)
 
 
 def make_material(m) -> rve_material:
@@ -224,7 +261,7 @@ class RVE:
     ``device``; the stream is torch's current stream on that device.
     """
 
-    def __init__(self, grain_id, quat, mat, L, device="cuda:0", stream=None, **options):
+    def __init__(self, grain_id, quat, mat, L, device="cuda:0", stream=None, own_stream=False, **options):
         import torch
         lib = load_library()
         if not torch.cuda.is_available():
@@ -245,7 +282,12 @@ class RVE:
             raise RVEError(RVE_EINVAL, f"unsupported grid {self.n} / grains {self.n_grains}")
         with torch.cuda.device(self.device):
             self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
-            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            if stream is not None:
+                self.stream = stream
+            elif own_stream:          # a stream of its own (concurrent batched steps)
+                self.stream = torch.cuda.Stream(self.device)
+            else:
+                self.stream = torch.cuda.current_stream(self.device)
         st, h = rve_create(gid, n0, n1, n2, q, self.n_grains, self.mat, self.opt, self.workspace.data_ptr(),
                            self.ws_bytes, self.stream.cuda_stream)
         if st != RVE_OK:
@@ -262,10 +304,13 @@ class RVE:
                       np.ascontiguousarray(mask, dtype=np.uint8).reshape(9),
                       np.ascontiguousarray(Pbar, dtype=np.float64).reshape(9), float(dt), info)
         out = dict(status=st, converged=bool(info.converged), newton_iters=info.newton_iters,
-                   cg_iters=list(info.cg_iters[:min(info.newton_iters, MAX_NEWTON_LOG)]),
+                   # a failed step also reports the Krylov iterations of the iteration that failed
+                   cg_iters=list(info.cg_iters[:min(info.newton_iters + (0 if info.converged else 1),
+                                                    MAX_NEWTON_LOG)]),
                    cg_iters_total=info.cg_iters_total, local_max_iters=info.local_max_iters,
                    local_failures=info.local_failures, halvings=info.halvings, residual=info.residual,
                    local_iters_total=info.local_iters_total, local_evals_total=info.local_evals_total,
+                   bicgstab_solves=info.bicgstab_solves,
                    residuals=list(info.residuals[:min(info.newton_iters, MAX_NEWTON_LOG) + 1]),
                    seconds=info.seconds)
         if check:

@@ -302,12 +302,26 @@ __device__ __forceinline__ void load_voxel(size_t nvox, size_t v, const int32_t*
   for (int a = 0; a < 12; ++a) in.tauc[a] = tauc_g[a * nvox + v];
 }
 
-// Local Newton on S (data-dependent iteration counts): writes S and dgam.
+// P = Fe S Fp^-T = F~ (Fp^-1 S Fp^-T) in the crystal frame, rotated to the
+// sample frame, with Fp^-1 = Fp_prev^-1 M^-1 (Eq. Piola)
+__device__ __forceinline__ void piola(const VoxelIn& in, const double* S, const double* Minv, double* P) {
+  double Fpinv[9], Sf[9], W[9], Q[9], Pt[9], U[9];
+  mat3_mul(in.Fpi0, Minv, Fpinv);
+  sym_full(S, Sf);
+  mat3_mult(Sf, Fpinv, W);
+  mat3_mul(Fpinv, W, Q);
+  mat3_mul(in.Ft, Q, Pt);
+  mat3_mult(Pt, in.R, U);
+  mat3_mul(in.R, U, P);
+}
+
+// Local Newton on S (data-dependent iteration counts): writes S, dgam and P.
 __global__ void __launch_bounds__(128) k_local(
     size_t nvox, const int32_t* __restrict__ grain, const double* __restrict__ grainR,
     const double* __restrict__ Fin, const double* __restrict__ xdir, double lambda,
     const double* __restrict__ Fp0inv, const double* __restrict__ tauc_g, const double* __restrict__ Swarm,
-    double* __restrict__ Sout, double* __restrict__ dgout, int32_t* __restrict__ counters, double dt, Consts c) {
+    double* __restrict__ Sout, double* __restrict__ dgout, double* __restrict__ Pout,
+    int32_t* __restrict__ counters, double dt, Consts c) {
   const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   int iters = 0, failed = 0, evals = 0;
   if (v < nvox) {
@@ -368,6 +382,10 @@ __global__ void __launch_bounds__(128) k_local(
     for (int k = 0; k < 6; ++k) Sout[k * nvox + v] = S[k];
 #pragma unroll
     for (int a = 0; a < 12; ++a) dgout[a * nvox + v] = e.dg[a];
+    double P[9];
+    piola(in, S, e.Minv, P);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Pout[k * nvox + v] = P[k];
   }
   // counters: warp-aggregated
   const unsigned full = 0xffffffffu;
@@ -386,13 +404,13 @@ __global__ void __launch_bounds__(128) k_local(
 }
 
 
-// P and the consistent tangent at the converged S: the same work for every
-// voxel (no data-dependent iterations), so whole warps stay converged.
+// The consistent tangent at the converged S: the same work for every voxel
+// (no data-dependent iterations), so whole warps stay converged.
 __global__ void __launch_bounds__(128) k_tangent(
     size_t nvox, const int32_t* __restrict__ grain, const double* __restrict__ grainR,
     const double* __restrict__ Fin, const double* __restrict__ xdir, double lambda,
     const double* __restrict__ Fp0inv, const double* __restrict__ tauc_g, const double* __restrict__ Sin,
-    double* __restrict__ Pout, double* __restrict__ Kout, double dt, Consts c, int k32) {
+    double* __restrict__ Kout, double dt, Consts c, int k32) {
   const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v < nvox) {
     VoxelIn in;
@@ -416,14 +434,6 @@ __global__ void __launch_bounds__(128) k_tangent(
     sym_full(S, Sf);
     mat3_mult(Sf, Fpinv, W);             // W = S Fpinv^T
     mat3_mul(Fpinv, W, Q);               // Q = Fpinv S Fpinv^T
-    {
-      double Pt[9], U[9], P[9];
-      mat3_mul(Ft, Q, Pt);
-      mat3_mult(Pt, R, U);               // P~ R^T
-      mat3_mul(R, U, P);                 // R P~ R^T
-#pragma unroll
-      for (int k = 0; k < 9; ++k) Pout[k * nvox + v] = P[k];
-    }
 #pragma unroll 1
     for (int kl = 0; kl < 9; ++kl) {
       const int kk = kl / 3, ll = kl % 3;
@@ -491,20 +501,29 @@ cudaError_t launch_hardening(const rve_s* h, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_constitutive(const rve_s* h, double dt, double lambda, int out_buf, int warm_buf,
-                                cudaStream_t s) {
+cudaError_t launch_local(const rve_s* h, double dt, double lambda, int out_buf, int warm_buf, cudaStream_t s) {
   const unsigned blocks = (unsigned)((h->nvox + 127) / 128);
   const double* warm = warm_buf < 0 ? h->S_c : h->S[warm_buf];
   {
     ProfScope ps_(h, RVE_K_CONSTITUTIVE, s);
     k_local<<<blocks, 128, 0, s>>>(h->nvox, h->grain, h->grainR, h->F, h->x, lambda, h->Fp0inv, h->tauc, warm,
-                                   h->S[out_buf], h->dgam[out_buf], h->dcount, dt, h->cst);
+                                   h->S[out_buf], h->dgam[out_buf], h->P[out_buf], h->dcount, dt, h->cst);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tangent(const rve_s* h, double dt, double lambda, int buf, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((h->nvox + 127) / 128);
   {
     ProfScope ps_(h, RVE_K_TANGENT_BUILD, s);
     k_tangent<<<blocks, 128, 0, s>>>(h->nvox, h->grain, h->grainR, h->F, h->x, lambda, h->Fp0inv, h->tauc,
-                                     h->S[out_buf], h->P[out_buf], h->K[out_buf], dt, h->cst,
-                                     h->opt.precision == 1);
+                                     h->S[buf], h->K[buf], dt, h->cst, h->opt.precision == 1);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_constitutive(const rve_s* h, double dt, double lambda, int out_buf, int warm_buf,
+                                cudaStream_t s) {
+  if (cudaError_t e = launch_local(h, dt, lambda, out_buf, warm_buf, s)) return e;
+  return launch_tangent(h, dt, lambda, out_buf, s);
 }

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -97,6 +98,8 @@ void carve(rve_s* h, Carver& c) {
   h->p = c.take<double>(9 * nv);
   h->t = c.take<double>(9 * nv);
   h->q = c.take<double>(9 * nv);
+  h->bv = c.take<double>(9 * nv);
+  h->bs = c.take<double>(9 * nv);
   h->spec = c.take<double2>(9 * h->nspec);
   if (h->opt.precision == 1) {
     for (int a = 0; a < 3; ++a) h->ax[a].tw32 = c.take<float2>(ns[a]);
@@ -254,12 +257,23 @@ rve_status run_project(rve_s* h, const double* in, double* out, const SpecParams
 // divergence stencil, scalar Laplace solve by FFT, gradient stencil; leaves
 // mean(X) in DS_XMEAN and sum Y^2 in DS_NORM.  Scratch: the first six
 // components of q (divergence, then the Laplace solution).
-rve_status run_project_stencil(rve_s* h, const double* X, double* Y, const uint8_t* mask, const double* shift) {
+// bits of the stress-controlled components: the zero mode keeps their means
+unsigned kept_means(const uint8_t* mask) {
+  unsigned m = 0;
+  for (int c = 0; c < 9; ++c)
+    if (!mask[c]) m |= 1u << c;
+  return m;
+}
+
+// all_means: reduce the means of all nine fields (the residual's scale is the
+// norm of the mean stress); otherwise only the kept ones
+rve_status run_project_stencil(rve_s* h, const double* X, double* Y, const uint8_t* mask, const double* shift,
+                               bool all_means = false) {
   double* d = h->q;
   double* u = h->q + 3 * h->nvox;
   SpecParams sp = project_params(h, mask, nullptr, nullptr);
   sp.op = OP_LAPINV;
-  RVE_CUDA(h, launch_div(h, X, d, 0, h->stream));
+  RVE_CUDA(h, launch_div(h, X, d, 0, all_means ? 0x1FFu : kept_means(mask), h->stream));
   RVE_CUDA(h, launch_fft_forward(h, d, h->stream, nullptr, 3));
   RVE_CUDA(h, launch_fft_op(h, sp, h->stream, nullptr, 3));
   RVE_CUDA(h, launch_fft_inverse(h, u, h->stream, nullptr, 3));
@@ -280,8 +294,8 @@ rve_status run_hardening(rve_s* h) {
 rve_status eval_residual(rve_s* h, double dt, double lambda, int out, int warm, const uint8_t* mask,
                          const double* Pbar_m, double* rabs, double* scale, int* lmax, int* lfail) {
   RVE_CUDA(h, cudaMemsetAsync(h->dcount, 0, 2 * sizeof(int32_t), h->stream));
-  RVE_CUDA(h, launch_constitutive(h, dt, lambda, out, warm, h->stream));
-  RVE_TRY(run_project_stencil(h, h->P[out], h->R, mask, Pbar_m));
+  RVE_CUDA(h, launch_local(h, dt, lambda, out, warm, h->stream));
+  RVE_TRY(run_project_stencil(h, h->P[out], h->R, mask, Pbar_m, true));
   RVE_TRY(read_scalars(h));
   *rabs = std::sqrt(h->hscal[DS_NORM] / (double)h->nvox);
   double pn = 0.0;
@@ -297,6 +311,69 @@ rve_status eval_residual(rve_s* h, double dt, double lambda, int out, int warm, 
 // at once after convergence), the host looks at the flag once per chunk.
 const int CG_CHUNK = 8;
 
+void release_graph(CgGraph& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g.exec = nullptr;
+  for (auto& p : g.rec.events) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  for (auto e : g.rec.spare) cudaEventDestroy(e);
+  g.rec = Prof::Capture();
+  g.cur = -1;
+}
+
+// Issue one full chunk of CG iterations.  With rve_options.graphs (and a
+// stream other than the legacy default stream, which cannot be captured) the
+// chunk is captured once per (tangent buffer, strain mask, profiling) into a
+// CUDA graph and replayed with a single launch: every launch of the chunk has
+// the same arguments and all iteration state lives on the device.  Up to
+// RVE_CG_GRAPHS captured chunks are kept per handle.
+template <class Issue>
+rve_status cg_chunk(rve_s* h, const uint8_t* mask, Issue issue) {
+  if (!h->opt.graphs || h->stream == nullptr) return issue();
+  const unsigned key = kept_means(mask);
+  CgGraph* g = nullptr;
+  for (auto& c : h->graphs)
+    if (c.exec && c.cur == h->cur && c.key == key && c.timed == h->prof.on) g = &c;
+  if (!g) {
+    g = &h->graphs[h->graph_next];
+    h->graph_next = (h->graph_next + 1) % RVE_CG_GRAPHS;
+    release_graph(*g);
+    if (h->prof.on) {
+      // two events per launch: created before the capture starts
+      for (int k = 0; k < 2 * 16 * CG_CHUNK; ++k) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) break;
+        g->rec.spare.push_back(e);
+      }
+    }
+    RVE_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    h->prof.cap = &g->rec;
+    const rve_status st = issue();
+    h->prof.cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(h->stream, &graph);
+    if (st != RVE_OK || ec != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      release_graph(*g);
+      if (st != RVE_OK) return st;
+      RVE_CUDA(h, ec);
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&g->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      g->exec = nullptr;
+      release_graph(*g);
+      RVE_CUDA(h, ei);
+    }
+    g->cur = h->cur;
+    g->key = key;
+    g->timed = h->prof.on;
+  }
+  RVE_CUDA(h, cudaGraphLaunch(g->exec, h->stream));
+  for (int c = 0; c < RVE_K_COUNT; ++c) h->prof.launches[c] += g->rec.launches[c];
+  if (g->timed) h->prof.borrowed.insert(h->prof.borrowed.end(), g->rec.events.begin(), g->rec.events.end());
+  return RVE_OK;
+}
+
 rve_status cg_solve(rve_s* h, const uint8_t* mask, double eta, int* iters, bool* ok) {
   RVE_CUDA(h, launch_cg_init(h, eta, h->stream));
   SpecParams sp = project_params(h, mask, nullptr, nullptr);
@@ -308,15 +385,19 @@ rve_status cg_solve(rve_s* h, const uint8_t* mask, double eta, int* iters, bool*
   *ok = false;
   while (issued < h->opt.max_cg) {
     const int chunk = std::min(CG_CHUNK, h->opt.max_cg - issued);
-    for (int i = 0; i < chunk; ++i) {
-      // t = K : p, then q = G*(t) as div -> Laplace solve -> grad fused with the update
-      RVE_CUDA(h, launch_tangent_apply(h, issued + i == 0, h->stream));
-      RVE_CUDA(h, launch_div(h, h->t, d, 1, h->stream));
-      RVE_CUDA(h, launch_fft_forward(h, d, h->stream, done, 3));
-      RVE_CUDA(h, launch_fft_op(h, sp, h->stream, done, 3));
-      RVE_CUDA(h, launch_fft_inverse(h, u, h->stream, done, 3));
-      RVE_CUDA(h, launch_grad_cg(h, u, mask, h->stream));
-    }
+    auto issue = [&]() -> rve_status {
+      for (int i = 0; i < chunk; ++i) {
+        // t = K : p, then q = G*(t) as div -> Laplace solve -> grad fused with the update
+        RVE_CUDA(h, launch_tangent_apply(h, h->stream));
+        RVE_CUDA(h, launch_div(h, h->t, d, 1, kept_means(mask), h->stream));
+        RVE_CUDA(h, launch_fft_forward(h, d, h->stream, done, 3));
+        RVE_CUDA(h, launch_fft_op(h, sp, h->stream, done, 3));
+        RVE_CUDA(h, launch_fft_inverse(h, u, h->stream, done, 3));
+        RVE_CUDA(h, launch_grad_cg(h, u, mask, h->stream));
+      }
+      return RVE_OK;
+    };
+    RVE_TRY(chunk == CG_CHUNK ? cg_chunk(h, mask, issue) : issue());
     issued += chunk;
     RVE_TRY(read_scalars(h));
     if (h->hscal[DS_DONE] != 0.0) break;
@@ -341,14 +422,18 @@ rve_status cg_solve32(rve_s* h, const uint8_t* mask, double eta, int* iters, boo
   *ok = false;
   while (issued < h->opt.max_cg) {
     const int chunk = std::min(CG_CHUNK, h->opt.max_cg - issued);
-    for (int i = 0; i < chunk; ++i) {
-      RVE_CUDA(h, launch_tangent_apply32(h, issued + i == 0, h->stream));
-      RVE_CUDA(h, launch_div32(h, h->t32, d, h->stream));
-      RVE_CUDA(h, launch_fft_forward32(h, d, h->stream, done));
-      RVE_CUDA(h, launch_fft_lapinv32(h, sp, h->stream, done));
-      RVE_CUDA(h, launch_fft_inverse32(h, u, h->stream, done));
-      RVE_CUDA(h, launch_grad_cg32(h, u, mask, h->stream));
-    }
+    auto issue = [&]() -> rve_status {
+      for (int i = 0; i < chunk; ++i) {
+        RVE_CUDA(h, launch_tangent_apply32(h, h->stream));
+        RVE_CUDA(h, launch_div32(h, h->t32, d, kept_means(mask), h->stream));
+        RVE_CUDA(h, launch_fft_forward32(h, d, h->stream, done));
+        RVE_CUDA(h, launch_fft_lapinv32(h, sp, h->stream, done));
+        RVE_CUDA(h, launch_fft_inverse32(h, u, h->stream, done));
+        RVE_CUDA(h, launch_grad_cg32(h, u, mask, h->stream));
+      }
+      return RVE_OK;
+    };
+    RVE_TRY(chunk == CG_CHUNK ? cg_chunk(h, mask, issue) : issue());
     issued += chunk;
     RVE_TRY(read_scalars(h));
     if (h->hscal[DS_DONE] != 0.0) break;
@@ -361,6 +446,79 @@ rve_status cg_solve32(rve_s* h, const uint8_t* mask, double eta, int* iters, boo
   // back in the range of G* (compatible fluctuation plus the stress-controlled
   // mean), so F stays compatible to FP64 round-off
   RVE_TRY(run_project_stencil(h, h->x, h->x, mask, nullptr));
+  return RVE_OK;
+}
+
+// BiCGStab (van der Vorst) on G*(K : x) = -R from x = 0, in FP64 (the
+// tangent is read as stored).  The consistent tangent is not symmetric; when
+// conjugate gradients stall on it (plastic onset in large RVEs) this is the
+// fallback.  r^ = r0 = -R.  Two operator applications and three host reads
+// of fused dot products per iteration.
+rve_status bicgstab_solve(rve_s* h, const uint8_t* mask, double eta, int* iters, bool* ok) {
+  cudaStream_t st = h->stream;
+  double* x = h->x; double* r = h->r; double* p = h->p; double* v = h->bv; double* sv = h->bs;
+  double* t = h->t;
+  const double* R = h->R;        // r^ = -R
+  auto dots = [&](int np, const double* a0, const double* b0, const double* a1, const double* b1,
+                  const double* a2, const double* b2, double* out) -> rve_status {
+    RVE_CUDA(h, launch_dots(h, np, a0, b0, a1, b1, a2, b2, DS_DOT, st));
+    RVE_TRY(read_scalars(h));
+    for (int k = 0; k < np; ++k) out[k] = h->hscal[DS_DOT + k];
+    return RVE_OK;
+  };
+  auto apply = [&](const double* in, double* out) -> rve_status {   // out = G*(K : in)
+    RVE_CUDA(h, launch_kmul(h, in, t, st));
+    RVE_TRY(run_project_stencil(h, t, out, mask, nullptr));
+    return RVE_OK;
+  };
+  RVE_CUDA(h, launch_lincomb(h, x, 0.0, R, 0.0, nullptr, 0.0, nullptr, st));
+  RVE_CUDA(h, launch_lincomb(h, r, -1.0, R, 0.0, nullptr, 0.0, nullptr, st));
+  RVE_CUDA(h, launch_lincomb(h, p, 0.0, R, 0.0, nullptr, 0.0, nullptr, st));
+  RVE_CUDA(h, launch_lincomb(h, v, 0.0, R, 0.0, nullptr, 0.0, nullptr, st));
+  double d[3];
+  RVE_TRY(dots(1, r, r, nullptr, nullptr, nullptr, nullptr, d));
+  const double stop = eta * eta * d[0];
+  double rho = 1.0, alpha = 1.0, omega = 1.0, rho_new = d[0];   // r^ . r0 = r0 . r0
+  *ok = !(d[0] > 0.0);
+  int k = 0;
+  for (; k < h->opt.max_cg && !*ok; ++k) {
+    if (rho_new == 0.0 || !std::isfinite(rho_new)) break;
+    const double beta = (rho_new / rho) * (alpha / omega);
+    RVE_CUDA(h, launch_lincomb(h, p, 1.0, r, beta, p, -beta * omega, v, st));     // p = r + beta (p - omega v)
+    RVE_TRY(apply(p, v));
+    RVE_TRY(dots(1, R, v, nullptr, nullptr, nullptr, nullptr, d));
+    const double rv = -d[0];
+    if (rv == 0.0 || !std::isfinite(rv)) break;
+    alpha = rho_new / rv;
+    RVE_CUDA(h, launch_lincomb(h, sv, 1.0, r, -alpha, v, 0.0, nullptr, st));      // s = r - alpha v
+    RVE_TRY(apply(sv, t));                                                        // t = A s (in place)
+    RVE_TRY(dots(3, t, sv, t, t, sv, sv, d));
+    if (!(d[2] > stop)) {                                                         // s small enough
+      RVE_CUDA(h, launch_lincomb(h, x, 1.0, x, alpha, p, 0.0, nullptr, st));
+      *ok = true;
+      ++k;
+      break;
+    }
+    if (!(d[1] > 0.0)) break;
+    omega = d[0] / d[1];
+    RVE_CUDA(h, launch_lincomb(h, x, 1.0, x, alpha, p, omega, sv, st));           // x += alpha p + omega s
+    RVE_CUDA(h, launch_lincomb(h, r, 1.0, sv, -omega, t, 0.0, nullptr, st));      // r = s - omega t
+    RVE_TRY(dots(2, R, r, r, r, nullptr, nullptr, d));
+    rho = rho_new;
+    rho_new = -d[0];
+    if (!(d[1] > stop)) { *ok = true; ++k; break; }
+    if (omega == 0.0) break;
+  }
+  *iters = k;
+  return RVE_OK;
+}
+
+// The tangent of the evaluation that ended the last increment, built on
+// request (rve_step skips it): same F, S, frozen hardening and step.
+rve_status build_stale_tangent(rve_s* h) {
+  if (!h->K_stale) return RVE_OK;
+  RVE_CUDA(h, launch_tangent(h, h->dt_prev, 0.0, h->cur, h->stream));
+  h->K_stale = false;
   return RVE_OK;
 }
 
@@ -396,6 +554,14 @@ cudaEvent_t Prof::take() {
 }
 
 void Prof::begin(int cat, cudaStream_t s, cudaEvent_t* a) {
+  if (cap) {
+    ++cap->launches[cat];
+    if (!on || cap->spare.size() < 2) return;
+    *a = cap->spare.back();
+    cap->spare.pop_back();
+    cudaEventRecordWithFlags(*a, s, cudaEventRecordExternal);
+    return;
+  }
   ++launches[cat];
   if (!on) return;
   *a = take();
@@ -404,6 +570,13 @@ void Prof::begin(int cat, cudaStream_t s, cudaEvent_t* a) {
 
 void Prof::end(int cat, cudaStream_t s, cudaEvent_t a) {
   if (!on || !a) return;
+  if (cap) {
+    cudaEvent_t b = cap->spare.back();
+    cap->spare.pop_back();
+    cudaEventRecordWithFlags(b, s, cudaEventRecordExternal);
+    cap->events.push_back({cat, a, b});
+    return;
+  }
   cudaEvent_t b = take();
   if (!b) { pool.push_back(a); return; }
   cudaEventRecord(b, s);
@@ -418,6 +591,11 @@ void Prof::resolve() {
     pool.push_back(p.b);
   }
   pending.clear();
+  for (auto& p : borrowed) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) ms[p.cat] += t;
+  }
+  borrowed.clear();
 }
 
 void Prof::reset() {
@@ -480,6 +658,8 @@ rve_status rve_create(const int32_t* grain_id, int n0, int n1, int n2, const dou
   h->mat = *mat;
   h->opt = *opt;
   h->stream = (cudaStream_t)cuda_stream;
+  h->device = 0;
+  cudaGetDevice(&h->device);
   h->h = opt->L / n0;
   h->mu = mat->mu > 0 ? mat->mu : 3.0 * mat->C44 * (mat->C11 - mat->C12) / (4.0 * mat->C44 + mat->C11 - mat->C12);
   h->cur = 0;
@@ -620,6 +800,7 @@ rve_status rve_step(rve_t* h, const double dFbar[9], const uint8_t strain_mask[9
     return st;
   };
   RVE_CUDA(h, cudaMemsetAsync(h->dcount + 8, 0, 4 * sizeof(int32_t), h->stream));
+  h->K_stale = false;
   rve_status st = run_hardening(h);
   if (st != RVE_OK) return finish(st);
   const int extrap = (h->opt.extrapolate && h->increment > 0) ? 1 : 0;
@@ -645,37 +826,71 @@ rve_status rve_step(rve_t* h, const double dFbar[9], const uint8_t strain_mask[9
     if (res <= h->opt.newton_tol) break;
     if (loc.newton_iters >= h->opt.max_newton)
       return finish(fail(h, RVE_ENOCONV_NEWTON, "Newton-Raphson reached max_newton"));
-    int ncg;
-    bool cgok;
+    // the tangent is built only at iterates that get a Krylov solve: not at
+    // rejected line-search trials, not at the iterate that ends the increment
+    if (cudaError_t e = launch_tangent(h, dt, 0.0, cur, h->stream)) {
+      h->err = cudaGetErrorString(e);
+      return finish(RVE_ECUDA);
+    }
+    int ncg = 0;
+    bool cgok = false;
     // inexact Newton: with cg_adaptive the linear solve only needs to be as
     // accurate as the current residual (forcing term min(1e-2, res)); the
     // converged increment does not depend on it
     const double eta = h->opt.cg_adaptive ? std::fmax(h->opt.cg_tol, std::fmin(1e-2, res)) : h->opt.cg_tol;
-    st = h->opt.precision == 1 ? cg_solve32(h, mask, eta, &ncg, &cgok) : cg_solve(h, mask, eta, &ncg, &cgok);
-    if (st != RVE_OK) return finish(st);
-    if (loc.newton_iters < RVE_MAX_NEWTON_LOG) loc.cg_iters[loc.newton_iters] = ncg;
-    loc.cg_iters_total += ncg;
-    // backtracking on phi(lam) = rms(R(F + lam dF))^2 with sufficient decrease;
-    // after a rejected trial the next lam minimises the quadratic through
-    // phi(0), the Newton slope -2 phi(0) and phi(lam), kept in [0.1, 0.5] lam
     double lam = 1.0, rt = 0.0, sct = 0.0;
     int lm = 0, lf = 0;
     bool acc = false;
-    const double f0 = rabs * rabs;
-    for (int hv = 0; hv <= h->opt.max_halvings; ++hv) {
-      st = eval_residual(h, dt, lam, 1 - cur, cur, mask, Pb, &rt, &sct, &lm, &lf);
-      if (st != RVE_OK) return finish(st);
-      if (lf == 0 && rt < rabs * (1.0 - 1e-4 * lam)) { acc = true; break; }
-      double next = 0.5 * lam;
-      if (lf == 0 && std::isfinite(rt)) {
-        const double c = (rt * rt - f0 * (1.0 - 2.0 * lam)) / (lam * lam);
-        if (c > 0.0) next = std::fmin(std::fmax(f0 / c, 0.1 * lam), 0.5 * lam);
+    // krylov 0: conjugate gradients (the paper's solver); when no step along
+    // the CG direction lowers the residual, the iteration is solved again with
+    // BiCGStab.  A CG solve cut off at max_cg still gives its direction a line
+    // search first: the truncated iterate is a damped step (CG iterates grow in
+    // norm from zero), which on an ill-conditioned tangent often does better
+    // than a fully solved BiCGStab step.  1: BiCGStab only; 2: CG only.
+    const int attempts = h->opt.krylov == 0 ? 2 : 1;
+    for (int att = 0; att < attempts && !acc; ++att) {
+      const bool use_bicg = h->opt.krylov == 1 || att == 1;
+      if (use_bicg) {
+        // trials of the rejected CG line search overwrote R: rebuild it from
+        // the current iterate's stress (its tangent K[cur] is untouched)
+        if (att == 1) RVE_TRY(run_project_stencil(h, h->P[cur], h->R, mask, Pb));
+        st = bicgstab_solve(h, mask, h->opt.precision == 1 ? std::fmax(eta, 1e-10) : eta, &ncg, &cgok);
+        ++loc.bicgstab_solves;
+      } else {
+        st = h->opt.precision == 1 ? cg_solve32(h, mask, eta, &ncg, &cgok) : cg_solve(h, mask, eta, &ncg, &cgok);
       }
-      lam = next;
-      ++loc.halvings;
+      if (st != RVE_OK) return finish(st);
+      if (loc.newton_iters < RVE_MAX_NEWTON_LOG) loc.cg_iters[loc.newton_iters] += ncg;
+      loc.cg_iters_total += ncg;
+      // backtracking on phi(lam) = rms(R(F + lam dF))^2 with sufficient decrease;
+      // after a rejected trial the next lam minimises the quadratic through
+      // phi(0), the Newton slope -2 phi(0) and phi(lam), kept in [0.1, 0.5] lam.
+      // A trial at which some voxel's local update fails (the step asks for
+      // slips above the local cap) is halved on a budget of its own: the
+      // current iterate itself has a converged local state, so a small enough
+      // step always passes.
+      lam = 1.0;
+      const double f0 = rabs * rabs;
+      int shrink = 0, local_cuts = 0;
+      while (shrink <= h->opt.max_halvings && local_cuts <= 40) {
+        st = eval_residual(h, dt, lam, 1 - cur, cur, mask, Pb, &rt, &sct, &lm, &lf);
+        if (st != RVE_OK) return finish(st);
+        if (lf == 0 && rt < rabs * (1.0 - 1e-4 * lam)) { acc = true; break; }
+        double next = 0.5 * lam;
+        if (lf == 0 && std::isfinite(rt)) {
+          const double c = (rt * rt - f0 * (1.0 - 2.0 * lam)) / (lam * lam);
+          if (c > 0.0) next = std::fmin(std::fmax(f0 / c, 0.1 * lam), 0.5 * lam);
+          ++shrink;
+        } else {
+          ++local_cuts;
+        }
+        lam = next;
+        ++loc.halvings;
+      }
     }
     if (!acc) {
       if (lf) return finish(fail(h, RVE_ENOCONV_LOCAL, "local update did not converge in the line search"));
+      if (!cgok) return finish(fail(h, RVE_ENOCONV_CG, "the Krylov solve did not converge"));
       return finish(fail(h, RVE_ENOCONV_NEWTON, "no step along the Newton direction lowers the residual"));
     }
     if (cudaError_t e = launch_axpy_F(h, lam, h->stream)) {
@@ -708,7 +923,39 @@ rve_status rve_step(rve_t* h, const double dFbar[9], const uint8_t strain_mask[9
   }
   h->dt_prev = dt;
   ++h->increment;
+  h->K_stale = true;
   return finish(RVE_OK);
+}
+
+rve_status rve_step_batch(rve_t* const* hs, int n, const double* dFbar, const uint8_t* strain_mask,
+                          const double* Pbar, const double* dt, rve_step_info* info, rve_status* status) {
+  if (!hs || n <= 0 || !dFbar || !strain_mask || !Pbar || !dt) return RVE_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return RVE_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return RVE_EINVAL;
+  }
+  std::vector<rve_status> st(n, RVE_OK);
+  auto run = [&](int i) {
+    cudaSetDevice(hs[i]->device);
+    st[i] = rve_step(hs[i], dFbar + 9 * i, strain_mask + 9 * i, Pbar + 9 * i, dt[i], info ? info + i : nullptr);
+  };
+  std::vector<std::thread> threads;
+  int started = 0;
+  try {
+    threads.reserve(n);
+    for (; started < n; ++started) threads.emplace_back(run, started);
+  } catch (...) {
+    // no more threads: the remaining handles run on this thread
+  }
+  for (int i = started; i < n; ++i) run(i);
+  for (auto& t : threads) t.join();
+  rve_status first = RVE_OK;
+  for (int i = 0; i < n; ++i) {
+    if (status) status[i] = st[i];
+    if (first == RVE_OK && st[i] != RVE_OK) first = st[i];
+  }
+  return first;
 }
 
 rve_status rve_get_macro_stress(rve_t* h, double P[9], double sigma[9]) {
@@ -736,6 +983,7 @@ rve_status rve_get_fields(rve_t* h, uint32_t which, void* dst, size_t bytes, int
     case RVE_FIELD_TAUC: src = h->tauc; break;
     case RVE_FIELD_DGAM: src = h->dgam[h->cur]; break;
     case RVE_FIELD_TANGENT:
+      RVE_TRY(build_stale_tangent(h));
       if (h->opt.precision == 1) {   // stored as float: widen into the other evaluation buffer
         double* tmp = h->K[1 - h->cur];
         RVE_CUDA(h, launch_widen(h, reinterpret_cast<const float*>(h->K[h->cur]), tmp, 81 * h->nvox, h->stream));
@@ -784,6 +1032,7 @@ rve_status rve_set_fields(rve_t* h, uint32_t which, const void* src, size_t byte
 
 rve_status rve_eval_hardening(rve_t* h) {
   if (!h) return RVE_EINVAL;
+  RVE_TRY(build_stale_tangent(h));   // before the frozen hardening state changes
   RVE_TRY(run_hardening(h));
   RVE_CUDA(h, cudaStreamSynchronize(h->stream));
   return RVE_OK;
@@ -795,6 +1044,7 @@ rve_status rve_eval_constitutive(rve_t* h, double dt, int32_t* local_max_iters, 
   RVE_CUDA(h, cudaMemcpyAsync(h->F, h->F_c, 9 * h->nvox * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   RVE_CUDA(h, cudaMemsetAsync(h->dcount, 0, 2 * sizeof(int32_t), h->stream));
   RVE_CUDA(h, launch_constitutive(h, dt, 0.0, h->cur, -1, h->stream));
+  h->K_stale = false;
   RVE_TRY(read_scalars(h));
   if (local_max_iters) *local_max_iters = h->hcount[0];
   if (local_failures) *local_failures = h->hcount[1];
@@ -862,6 +1112,7 @@ rve_status rve_restore(rve_t* h, const void* host_buf, size_t bytes) {
   RVE_CUDA(h, cudaMemcpyAsync(h->P[0], h->P_c, 9 * h->nvox * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   RVE_CUDA(h, cudaStreamSynchronize(h->stream));
   h->cur = 0;
+  h->K_stale = false;
   h->increment = hd.increment;
   h->dt_prev = hd.dt_prev;
   for (int c = 0; c < 9; ++c) { h->dFbar_prev[c] = hd.dFbar_prev[c]; h->Pmacro[c] = hd.Pmacro[c]; h->Smacro[c] = hd.Smacro[c]; }
@@ -892,6 +1143,7 @@ const char* rve_last_error(const rve_t* h) { return h ? h->err.c_str() : "null h
 void rve_destroy(rve_t* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  for (auto& g : h->graphs) release_graph(g);
   h->prof.destroy();
   cudaFreeHost(h->hscal);
   cudaFreeHost(h->hcount);

@@ -62,6 +62,16 @@ struct Prof {
   struct Pending { int cat; cudaEvent_t a, b; };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
+  // A stream capture in progress records into `cap`: launch counts per
+  // category, and (when timing) event pairs taken from its spare events and
+  // recorded as external event nodes of the graph.  The graph owns them.
+  struct Capture {
+    int64_t launches[RVE_K_COUNT] = {0};
+    std::vector<Pending> events;
+    std::vector<cudaEvent_t> spare;
+  };
+  Capture* cap = nullptr;
+  std::vector<Pending> borrowed;   // graph-owned pairs replayed since the last resolve
   cudaEvent_t take();
   void begin(int cat, cudaStream_t s, cudaEvent_t* a);
   void end(int cat, cudaStream_t s, cudaEvent_t a);
@@ -69,6 +79,16 @@ struct Prof {
   void reset();
   void destroy();
 };
+
+// One captured chunk of CG iterations (see cg_chunk in rve_api.cu).
+struct CgGraph {
+  cudaGraphExec_t exec = nullptr;
+  int cur = -1;            // tangent buffer the chunk reads
+  unsigned key = 0;        // strain mask bits
+  bool timed = false;      // captured with profiling events
+  Prof::Capture rec;
+};
+constexpr int RVE_CG_GRAPHS = 4;
 
 struct rve_s {
   int n0, n1, n2, nkx;
@@ -79,6 +99,7 @@ struct rve_s {
   double mu, h;
   Consts cst;
   cudaStream_t stream;
+  int device;           // CUDA device current at rve_create
   FFTPlan plan[3];
   AxisTables ax[3];
 
@@ -93,7 +114,11 @@ struct rve_s {
   double* F;            // Newton iterate
   double *P[2], *K[2], *S[2], *dgam[2];             // evaluation double buffer
   int cur;
+  bool K_stale = false;   // the converged evaluation's tangent is not built yet (built on request)
+  CgGraph graphs[RVE_CG_GRAPHS];
+  int graph_next = 0;
   double *R, *x, *r, *p, *t, *q;
+  double *bv, *bs;      // BiCGStab vectors v and s
   double2* spec;        // 9 * nspec
   // mixed precision (precision == 1): FP32 conjugate-gradient state
   float2* spec32;       // 3 * nspec
@@ -123,7 +148,7 @@ struct ProfScope {
 // device scalar slots
 enum { DS_RR = 0, DS_PKP = 1, DS_ALPHA = 2, DS_BETA = 3, DS_NORM = 4, DS_STOP = 5, DS_DONE = 6, DS_ITERS = 7,
        DS_MEANP = 8,
-       DS_MEANSIG = 17, DS_MEANF = 26, DS_XMEAN = 48 };
+       DS_MEANSIG = 17, DS_MEANF = 26, DS_DOT = 35, DS_XMEAN = 48 };
 
 // ---- fft.cu ----
 // `done` (nullable, device): when *done != 0 every block returns at once (the
@@ -141,28 +166,42 @@ cudaError_t launch_fft_lapinv32(const rve_s* h, const SpecParams& sp, cudaStream
 cudaError_t launch_fft_inverse32(const rve_s* h, float* out, cudaStream_t s, const double* done);
 
 // ---- stencil.cu: G* = D (D^H D)^-1 D^H with real-space rotated-scheme stencils ----
-cudaError_t launch_div(const rve_s* h, const double* X, double* d, int check_done, cudaStream_t s);
+// mean_mask: bit c set = the mean of field c is reduced into ds[DS_XMEAN + c]
+// (others read 0)
+cudaError_t launch_div(const rve_s* h, const double* X, double* d, int check_done, unsigned mean_mask,
+                       cudaStream_t s);
 cudaError_t launch_grad(const rve_s* h, const double* u, double* Y, const uint8_t* mask, const double* shift,
                         cudaStream_t s);
 cudaError_t launch_grad_cg(const rve_s* h, const double* u, const uint8_t* mask, cudaStream_t s);
-cudaError_t launch_div32(const rve_s* h, const float* X, float* d, cudaStream_t s);
+cudaError_t launch_div32(const rve_s* h, const float* X, float* d, unsigned mean_mask, cudaStream_t s);
 cudaError_t launch_grad_cg32(const rve_s* h, const float* u, const uint8_t* mask, cudaStream_t s);
 
 // ---- constitutive.cu ----
 cudaError_t launch_hardening(const rve_s* h, cudaStream_t s);
+// local update (S, dgam, P) at F + lambda x into buffer out_buf, warm-started
+// from S[warm_buf] (or the committed S when warm_buf < 0)
+cudaError_t launch_local(const rve_s* h, double dt, double lambda, int out_buf, int warm_buf, cudaStream_t s);
+// consistent tangent K[buf] at F + lambda x and the converged S[buf]
+cudaError_t launch_tangent(const rve_s* h, double dt, double lambda, int buf, cudaStream_t s);
+// both
 cudaError_t launch_constitutive(const rve_s* h, double dt, double lambda, int out_buf, int warm_buf,
                                 cudaStream_t s);
 
 // ---- vec.cu ----
-cudaError_t launch_tangent_apply(const rve_s* h, int first, cudaStream_t s);
+cudaError_t launch_tangent_apply(const rve_s* h, cudaStream_t s);
 cudaError_t launch_cg_update(const rve_s* h, cudaStream_t s);
 cudaError_t launch_norm2(const rve_s* h, const double* a, int ncomp, cudaStream_t s);
 cudaError_t launch_reduce_final(const rve_s* h, int mode, cudaStream_t s);
 cudaError_t launch_cg_init(const rve_s* h, double eta, cudaStream_t s);
-cudaError_t launch_tangent_apply32(const rve_s* h, int first, cudaStream_t s);
+cudaError_t launch_tangent_apply32(const rve_s* h, cudaStream_t s);
 cudaError_t launch_cg_init32(const rve_s* h, double eta, cudaStream_t s);
 cudaError_t launch_widen_x(const rve_s* h, cudaStream_t s);
 cudaError_t launch_widen(const rve_s* h, const float* a, double* b, size_t n, cudaStream_t s);
+cudaError_t launch_kmul(const rve_s* h, const double* in, double* out, cudaStream_t s);
+cudaError_t launch_dots(const rve_s* h, int np, const double* a0, const double* b0, const double* a1,
+                        const double* b1, const double* a2, const double* b2, int slot, cudaStream_t s);
+cudaError_t launch_lincomb(const rve_s* h, double* out, double c0, const double* a0, double c1, const double* a1,
+                           double c2, const double* a2, cudaStream_t s);
 cudaError_t launch_axpy_F(const rve_s* h, double lambda, cudaStream_t s);
 cudaError_t launch_predictor(const rve_s* h, const double* dFb, const double* dFb_prev, double ratio,
                              int extrapolate, cudaStream_t s);

@@ -50,12 +50,14 @@ template <typename V>
 __global__ void __launch_bounds__(NT) k_div(Grid3 g, Tiling T, const V* __restrict__ X,
                                            V* __restrict__ d, double* __restrict__ ds,
                                            double* __restrict__ partial, unsigned int* __restrict__ ticket,
-                                           int check_done) {
+                                           int check_done, unsigned mean_mask) {
   __shared__ V S[9][SMAX];
   __shared__ double sh[32];
   if (check_done && ds[DS_DONE] != 0.0) return;
   const int W = T.tx + 1;     // row pitch of the staged tile (with its halo)
   const int tx = threadIdx.x, ty = threadIdx.y;
+  const int lt = tx + T.tx * ty;
+  const int H = T.tx + 1 + T.ty;   // halo: row y0 - 1 (x0 - 1 .. x0 + tx - 1), column x0 - 1
   const unsigned plane = (unsigned)g.n0 * g.n1;
   V mean[9];
 #pragma unroll
@@ -65,29 +67,39 @@ __global__ void __launch_bounds__(NT) k_div(Grid3 g, Tiling T, const V* __restri
     const int x0 = bxi * T.tx, y0 = byi * T.ty;
     const int x = x0 + tx, y = y0 + ty;
     const bool inside = y < g.n1;
-    const int xh = wrapi(x0 - 1, g.n0), yh = wrapi(y0 - 1, g.n1), ym = inside ? y : 0;
+    const int ym = inside ? y : 0;
     const int zp = wrapi(z - 1, g.n2);
     const unsigned rz = (unsigned)z * plane, rzp = (unsigned)zp * plane;
-    const unsigned own = (unsigned)ym * g.n0 + x, hrow = (unsigned)yh * g.n0 + x;
-    const unsigned hcol = (unsigned)ym * g.n0 + xh, hcor = (unsigned)yh * g.n0 + xh;
+    const unsigned own = (unsigned)ym * g.n0 + x;
 #pragma unroll
     for (int f = 0; f < 9; ++f) {
       const V* F = X + (size_t)f * g.nvox;
       const bool diff = (f % 3) == 2;      // the z-derivative field of each row
       const V a = __ldg(F + rz + own), bm = __ldg(F + rzp + own);
       S[f][(ty + 1) * W + tx + 1] = diff ? bm - a : a + bm;
-      if (inside) mean[f] += a;
-      if (ty == 0) {
-        const V a2 = __ldg(F + rz + hrow), b2 = __ldg(F + rzp + hrow);
-        S[f][tx + 1] = diff ? b2 - a2 : a2 + b2;
+      if (inside && ((mean_mask >> f) & 1u)) mean[f] += a;
+    }
+    // the halo is spread over the first H linear threads (whole warps), not
+    // given to one lane of every warp: a divergent FP64 instruction costs the
+    // pipe as much as a full one
+    for (int hh = lt; hh < H; hh += NT) {
+      int sidx, gx, gy;
+      if (hh <= T.tx) {
+        sidx = hh;
+        gx = wrapi(x0 - 1 + hh, g.n0);
+        gy = wrapi(y0 - 1, g.n1);
+      } else {
+        const int j = hh - T.tx - 1;
+        sidx = (j + 1) * W;
+        gx = wrapi(x0 - 1, g.n0);
+        gy = (y0 + j < g.n1) ? y0 + j : 0;   // rows past n1 are never a neighbour here
       }
-      if (tx == 0) {
-        const V a3 = __ldg(F + rz + hcol), b3 = __ldg(F + rzp + hcol);
-        S[f][(ty + 1) * W] = diff ? b3 - a3 : a3 + b3;
-        if (ty == 0) {
-          const V a4 = __ldg(F + rz + hcor), b4 = __ldg(F + rzp + hcor);
-          S[f][0] = diff ? b4 - a4 : a4 + b4;
-        }
+      const unsigned o = (unsigned)gy * g.n0 + gx;
+#pragma unroll
+      for (int f = 0; f < 9; ++f) {
+        const V* F = X + (size_t)f * g.nvox;
+        const V a = __ldg(F + rz + o), bm = __ldg(F + rzp + o);
+        S[f][sidx] = (f % 3) == 2 ? bm - a : a + bm;
       }
     }
     __syncthreads();
@@ -110,6 +122,10 @@ __global__ void __launch_bounds__(NT) k_div(Grid3 g, Tiling T, const V* __restri
   }
 #pragma unroll
   for (int c = 0; c < 9; ++c) {
+    if (!((mean_mask >> c) & 1u)) {          // not needed: a zero partial
+      if (tx == 0 && ty == 0) partial[(size_t)c * gridDim.x + blockIdx.x] = 0.0;
+      continue;
+    }
     const double s = blk_sum((double)mean[c], sh);
     if (tx == 0 && ty == 0) partial[(size_t)c * gridDim.x + blockIdx.x] = s;
   }
@@ -142,6 +158,8 @@ __global__ void __launch_bounds__(NT) k_grad_t(Grid3 g, Tiling T, const V* __res
   for (int c = 0; c < 9; ++c) off[c] = zm.keep[c] ? (V)(ds[DS_XMEAN + c] + zm.add[c]) : (V)0;
   const int W = T.tx + 1;
   const int tx = threadIdx.x, ty = threadIdx.y;
+  const int lt = tx + T.tx * ty;
+  const int H = T.tx + 1 + T.ty;
   const unsigned plane = (unsigned)g.n0 * g.n1;
   V acc = (V)0;
   for (int t = blockIdx.x; t < T.ntiles; t += gridDim.x) {
@@ -155,28 +173,35 @@ __global__ void __launch_bounds__(NT) k_grad_t(Grid3 g, Tiling T, const V* __res
     const int xh = wrapi(x0 + T.tx, g.n0), yh = (y0 + T.ty) % g.n1, ym = inside ? yi : 0;
     const int zn = wrapi(z + 1, g.n2);
     const unsigned rz = (unsigned)z * plane, rzn = (unsigned)zn * plane;
-    const unsigned own = (unsigned)ym * g.n0 + xi, hrow = (unsigned)yh * g.n0 + xi;
-    const unsigned hcol = (unsigned)ym * g.n0 + xh, hcor = (unsigned)yh * g.n0 + xh;
+    const unsigned own = (unsigned)ym * g.n0 + xi;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const V* F = u + (size_t)i * g.nvox;
       const V a = __ldg(F + rz + own), c = __ldg(F + rzn + own);
       SP[i][ty * W + tx] = a + c;
       SM[i][ty * W + tx] = c - a;
-      if (ty == T.ty - 1) {
-        const V a2 = __ldg(F + rz + hrow), c2 = __ldg(F + rzn + hrow);
-        SP[i][T.ty * W + tx] = a2 + c2;
-        SM[i][T.ty * W + tx] = c2 - a2;
+    }
+    // high halo (row y0 + ty: x0 .. x0 + tx, the last one the corner; column
+    // x0 + tx), spread over the first H linear threads
+    for (int hh = lt; hh < H; hh += NT) {
+      int sidx, gx, gy;
+      if (hh <= T.tx) {
+        sidx = T.ty * W + hh;
+        gx = hh < T.tx ? x0 + hh : xh;
+        gy = yh;
+      } else {
+        const int j = hh - T.tx - 1;
+        sidx = j * W + T.tx;
+        gx = xh;
+        gy = (y0 + j < g.n1) ? y0 + j : 0;   // row n1 wraps to row 0
       }
-      if (tx == T.tx - 1) {
-        const V a3 = __ldg(F + rz + hcol), c3 = __ldg(F + rzn + hcol);
-        SP[i][ty * W + T.tx] = a3 + c3;
-        SM[i][ty * W + T.tx] = c3 - a3;
-        if (ty == T.ty - 1) {
-          const V a4 = __ldg(F + rz + hcor), c4 = __ldg(F + rzn + hcor);
-          SP[i][T.ty * W + T.tx] = a4 + c4;
-          SM[i][T.ty * W + T.tx] = c4 - a4;
-        }
+      const unsigned o = (unsigned)gy * g.n0 + gx;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const V* F = u + (size_t)i * g.nvox;
+        const V a = __ldg(F + rz + o), c = __ldg(F + rzn + o);
+        SP[i][sidx] = a + c;
+        SM[i][sidx] = c - a;
       }
     }
     __syncthreads();
@@ -254,13 +279,15 @@ ZeroMode zero_mode(const uint8_t* mask, const double* shift) {
 
 }  // namespace
 
-cudaError_t launch_div(const rve_s* h, const double* X, double* d, int check_done, cudaStream_t s) {
+cudaError_t launch_div(const rve_s* h, const double* X, double* d, int check_done, unsigned mean_mask,
+                       cudaStream_t s) {
   Tiling T = tiling_of(h);
+  if ((T.tx + 1) * (T.ty + 1) > SMAX) return cudaErrorInvalidValue;   // n0 odd: not a valid grid
   if (T.nblocks > DIV_BLOCKS) T.nblocks = DIV_BLOCKS;
   {
     ProfScope ps_(h, RVE_K_STENCIL, s);
     k_div<double><<<T.nblocks, dim3(T.tx, T.ty), 0, s>>>(grid_of(h), T, X, d, h->dscal, h->partial,
-                                                         (unsigned int*)(h->dcount + 4), check_done);
+                                                         (unsigned int*)(h->dcount + 4), check_done, mean_mask);
   }
   return cudaGetLastError();
 }
@@ -268,6 +295,7 @@ cudaError_t launch_div(const rve_s* h, const double* X, double* d, int check_don
 cudaError_t launch_grad(const rve_s* h, const double* u, double* Y, const uint8_t* mask, const double* shift,
                         cudaStream_t s) {
   const Tiling T = tiling_of(h);
+  if ((T.tx + 1) * (T.ty + 1) > SMAX) return cudaErrorInvalidValue;   // n0 odd: not a valid grid
   {
     ProfScope ps_(h, RVE_K_STENCIL, s);
     k_grad_t<false, double><<<T.nblocks, dim3(T.tx, T.ty), 0, s>>>(grid_of(h), T, u, zero_mode(mask, shift), Y,
@@ -279,6 +307,7 @@ cudaError_t launch_grad(const rve_s* h, const double* u, double* Y, const uint8_
 
 cudaError_t launch_grad_cg(const rve_s* h, const double* u, const uint8_t* mask, cudaStream_t s) {
   const Tiling T = tiling_of(h);
+  if ((T.tx + 1) * (T.ty + 1) > SMAX) return cudaErrorInvalidValue;   // n0 odd: not a valid grid
   {
     ProfScope ps_(h, RVE_K_CG_UPDATE, s);
     k_grad_t<true, double><<<T.nblocks, dim3(T.tx, T.ty), 0, s>>>(grid_of(h), T, u, zero_mode(mask, nullptr),
@@ -288,19 +317,21 @@ cudaError_t launch_grad_cg(const rve_s* h, const double* u, const uint8_t* mask,
   return cudaGetLastError();
 }
 
-cudaError_t launch_div32(const rve_s* h, const float* X, float* d, cudaStream_t s) {
+cudaError_t launch_div32(const rve_s* h, const float* X, float* d, unsigned mean_mask, cudaStream_t s) {
   Tiling T = tiling_of(h);
+  if ((T.tx + 1) * (T.ty + 1) > SMAX) return cudaErrorInvalidValue;   // n0 odd: not a valid grid
   if (T.nblocks > DIV_BLOCKS) T.nblocks = DIV_BLOCKS;
   {
     ProfScope ps_(h, RVE_K_STENCIL, s);
     k_div<float><<<T.nblocks, dim3(T.tx, T.ty), 0, s>>>(grid_of(h), T, X, d, h->dscal, h->partial,
-                                                        (unsigned int*)(h->dcount + 4), 1);
+                                                        (unsigned int*)(h->dcount + 4), 1, mean_mask);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_grad_cg32(const rve_s* h, const float* u, const uint8_t* mask, cudaStream_t s) {
   const Tiling T = tiling_of(h);
+  if ((T.tx + 1) * (T.ty + 1) > SMAX) return cudaErrorInvalidValue;   // n0 odd: not a valid grid
   {
     ProfScope ps_(h, RVE_K_CG_UPDATE, s);
     k_grad_t<true, float><<<T.nblocks, dim3(T.tx, T.ty), 0, s>>>(grid_of(h), T, u, zero_mode(mask, nullptr), nullptr,

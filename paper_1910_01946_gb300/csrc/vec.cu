@@ -45,10 +45,14 @@ __device__ __forceinline__ double last_block_sum(const double* partial, unsigned
 __global__ void __launch_bounds__(RVE_RED_THREADS, 2) k_tangent_apply(size_t nvox, const double* __restrict__ K,
                                                                       const double* __restrict__ r, double* __restrict__ p,
                                                                       double* __restrict__ t, double* __restrict__ ds,
-                                                                      int first, double* __restrict__ partial,
+                                                                      double* __restrict__ partial,
                                                                       unsigned int* __restrict__ ticket) {
   __shared__ double sh[32];
   if (ds[DS_DONE] != 0.0) return;
+  // the first iteration of a solve (the counter is reset by the CG init and
+  // bumped by each completed iteration): every launch of the loop has the
+  // same arguments, so chunks of iterations can be replayed as a CUDA graph
+  const bool first = ds[DS_ITERS] == 0.0;
   const double beta = first ? 0.0 : ds[DS_BETA];
   double acc = 0.0;
   for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (size_t)gridDim.x * blockDim.x) {
@@ -116,10 +120,11 @@ __global__ void __launch_bounds__(RVE_RED_THREADS) k_cg_update(size_t n, double*
 __global__ void __launch_bounds__(RVE_RED_THREADS) k_tangent_apply32(size_t nvox, const float* __restrict__ K,
                                                                      const float* __restrict__ r, float* __restrict__ p,
                                                                      float* __restrict__ t, double* __restrict__ ds,
-                                                                     int first, double* __restrict__ partial,
+                                                                     double* __restrict__ partial,
                                                                      unsigned int* __restrict__ ticket) {
   __shared__ double sh[32];
   if (ds[DS_DONE] != 0.0) return;
+  const bool first = ds[DS_ITERS] == 0.0;
   const float beta = first ? 0.0f : (float)ds[DS_BETA];
   float acc = 0.0f;
   for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (size_t)gridDim.x * blockDim.x) {
@@ -381,11 +386,11 @@ unsigned grid_for(size_t n, int threads) {
 
 }  // namespace
 
-cudaError_t launch_tangent_apply(const rve_s* h, int first, cudaStream_t s) {
+cudaError_t launch_tangent_apply(const rve_s* h, cudaStream_t s) {
   {
     ProfScope ps_(h, RVE_K_TANGENT_APPLY, s);
     k_tangent_apply<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, h->K[h->cur], h->r, h->p, h->t, h->dscal,
-                                                               first, h->partial, (unsigned int*)(h->dcount + 4));
+                                                               h->partial, (unsigned int*)(h->dcount + 4));
   }
   return cudaGetLastError();
 }
@@ -418,11 +423,16 @@ cudaError_t launch_norm2(const rve_s* h, const double* a, int ncomp, cudaStream_
   return launch_reduce_final(h, RED_NORM, s);
 }
 
+// k_macro reduces 27 values per thread at the end (five shuffle additions
+// each, FP64): one block per SM amortises that over many voxels
+constexpr int MACRO_BLOCKS = 152;
+
 cudaError_t launch_reduce_final(const rve_s* h, int mode, cudaStream_t s) {
   const int nval = mode == RED_MACRO ? 27 : 1;
+  const int nparts = mode == RED_MACRO ? MACRO_BLOCKS : RVE_RED_BLOCKS;
   {
     ProfScope ps_(h, RVE_K_REDUCE, s);
-    k_reduce_final<<<1, 1024, 0, s>>>(h->partial, RVE_RED_BLOCKS, nval, mode, h->dscal);
+    k_reduce_final<<<1, 1024, 0, s>>>(h->partial, nparts, nval, mode, h->dscal);
   }
   return cudaGetLastError();
 }
@@ -459,7 +469,7 @@ cudaError_t launch_commit(const rve_s* h, cudaStream_t s) {
 cudaError_t launch_macro(const rve_s* h, cudaStream_t s) {
   {
     ProfScope ps_(h, RVE_K_REDUCE, s);
-    k_macro<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, h->P_c, h->F_c, h->partial);
+    k_macro<<<MACRO_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, h->P_c, h->F_c, h->partial);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -475,11 +485,11 @@ cudaError_t launch_output_field(const rve_s* h, int which, const double* P, cons
   return cudaGetLastError();
 }
 
-cudaError_t launch_tangent_apply32(const rve_s* h, int first, cudaStream_t s) {
+cudaError_t launch_tangent_apply32(const rve_s* h, cudaStream_t s) {
   {
     ProfScope ps_(h, RVE_K_TANGENT_APPLY, s);
     k_tangent_apply32<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, reinterpret_cast<const float*>(h->K[h->cur]),
-                                                                 h->r32, h->p32, h->t32, h->dscal, first, h->partial,
+                                                                 h->r32, h->p32, h->t32, h->dscal, h->partial,
                                                                  (unsigned int*)(h->dcount + 4));
   }
   return cudaGetLastError();
@@ -506,6 +516,93 @@ cudaError_t launch_widen(const rve_s* h, const float* a, double* b, size_t n, cu
   {
     ProfScope ps_(h, RVE_K_OTHER, s);
     k_widen<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(n, a, b);
+  }
+  return cudaGetLastError();
+}
+
+// ---- BiCGStab support (FP64): w = K : v; fused dot products; linear combinations
+namespace {
+
+template <typename KT>
+__global__ void __launch_bounds__(RVE_RED_THREADS, 2) k_kmul(size_t nvox, const KT* __restrict__ K,
+                                                             const double* __restrict__ in, double* __restrict__ out) {
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (size_t)gridDim.x * blockDim.x) {
+    double pv[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) pv[k] = in[k * nvox + v];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      double s = 0.0;
+#pragma unroll
+      for (int j = 0; j < 9; ++j) s = fma((double)__ldcs(K + (size_t)(9 * i + j) * nvox + v), pv[j], s);
+      out[i * nvox + v] = s;
+    }
+  }
+}
+
+// up to three dot products a_k . b_k at once -> ds[slot + k]
+__global__ void __launch_bounds__(RVE_RED_THREADS) k_dots(size_t n, int np, const double* __restrict__ a0,
+                                                          const double* __restrict__ b0, const double* __restrict__ a1,
+                                                          const double* __restrict__ b1, const double* __restrict__ a2,
+                                                          const double* __restrict__ b2, double* __restrict__ ds,
+                                                          int slot, double* __restrict__ partial,
+                                                          unsigned int* __restrict__ ticket) {
+  __shared__ double sh[32];
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    acc[0] = fma(a0[e], b0[e], acc[0]);
+    if (np > 1) acc[1] = fma(a1[e], b1[e], acc[1]);
+    if (np > 2) acc[2] = fma(a2[e], b2[e], acc[2]);
+  }
+  for (int c = 0; c < np; ++c) {
+    const double s = blk_sum(acc[c], sh);
+    if (threadIdx.x == 0) partial[(size_t)c * gridDim.x + blockIdx.x] = s;
+  }
+  double tot[3];
+  if (last_block_sums(partial, np, ticket, sh, tot) && threadIdx.x == 0)
+    for (int c = 0; c < np; ++c) ds[slot + c] = tot[c];
+}
+
+// out = c0 a0 + c1 a1 + c2 a2 (a1, a2 nullable; out may alias an input)
+__global__ void k_lincomb(size_t n, double* out, double c0, const double* a0, double c1, const double* a1,
+                          double c2, const double* a2) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double v = c0 * a0[e];
+    if (a1) v = fma(c1, a1[e], v);
+    if (a2) v = fma(c2, a2[e], v);
+    out[e] = v;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_kmul(const rve_s* h, const double* in, double* out, cudaStream_t s) {
+  {
+    ProfScope ps_(h, RVE_K_TANGENT_APPLY, s);
+    if (h->opt.precision == 1)   // the tangent is stored as float in mixed precision
+      k_kmul<float><<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, reinterpret_cast<const float*>(h->K[h->cur]),
+                                                               in, out);
+    else
+      k_kmul<double><<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, h->K[h->cur], in, out);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dots(const rve_s* h, int np, const double* a0, const double* b0, const double* a1,
+                        const double* b1, const double* a2, const double* b2, int slot, cudaStream_t s) {
+  {
+    ProfScope ps_(h, RVE_K_REDUCE, s);
+    k_dots<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(9 * h->nvox, np, a0, b0, a1, b1, a2, b2, h->dscal, slot,
+                                                      h->partial, (unsigned int*)(h->dcount + 4));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lincomb(const rve_s* h, double* out, double c0, const double* a0, double c1, const double* a1,
+                           double c2, const double* a2, cudaStream_t s) {
+  {
+    ProfScope ps_(h, RVE_K_OTHER, s);
+    k_lincomb<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(9 * h->nvox, out, c0, a0, c1, a1, c2, a2);
   }
   return cudaGetLastError();
 }

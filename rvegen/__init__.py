@@ -173,3 +173,18 @@ WORKLOADS = {
     "cu64": Workload("cu64_100g_5pct_50inc", 64, 100, "Cu", 0.05, 50, seed=1001),
     "al128": Workload("al128_500g_3pct_30inc", 128, 500, "Al", 0.03, 30, seed=1002),
 }
+
+
+def sweep_workloads():
+    """The batched grain-size sweep: 16 RVEs j = 0..15 with edge
+    {32, 48, 64, 96}[j // 4] voxels, n_j = round(8 * 50^(j/15)) grains (8 to
+    400, log-spaced), materials Cu, Al, Ag, Ni cycled, a fixed 100 um edge (so
+    the mean grain size falls from about 62 to 17 um), tension to 2 % in 20
+    increments at 1e-3 /s, seeds 1300 + j."""
+    out = []
+    for j in range(16):
+        n = (32, 48, 64, 96)[j // 4]
+        g = int(round(8 * 50 ** (j / 15.0)))
+        out.append(Workload(f"sweep{j:02d}_{n}_{g}g_{('Cu', 'Al', 'Ag', 'Ni')[j % 4]}", n, g,
+                            ("Cu", "Al", "Ag", "Ni")[j % 4], 0.02, 20, seed=1300 + j, L=100e-6))
+    return out

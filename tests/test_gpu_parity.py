@@ -251,3 +251,23 @@ def test_mixed_precision_matches_fp64_path_cu16(pkg):
         assert relerr(b.field(name), a.field(name)) < 1e-9, name
     assert relerr(b.macro_stress()[0], a.macro_stress()[0]) < 1e-9
     a.close(); b.close()
+
+
+@pytest.mark.parametrize("wl", [rvegen.Workload("cu8", 8, 5, "Cu", 0.004, 4, seed=31)], ids=["cu8x4"])
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_bicgstab_increments_match_oracle(pkg, wl, precision):
+    """krylov = 1 solves every Newton step with BiCGStab instead of CG; the
+    converged increment is the same one the oracle's CG path reaches."""
+    gid, quat, mat = wl.inputs()
+    g = pkg.RVE(gid, quat, mat, wl.edge, krylov=1, precision=precision)
+    o = solver.RVE(gid, quat, mat, wl.edge)
+    for k in range(wl.increments):
+        gi = g.step(wl.dFbar(), MASK, np.zeros(9), wl.dt)
+        oi = o.step(wl.dFbar(), MASK, np.zeros(9), wl.dt)
+        assert gi["converged"] and oi.converged
+        assert gi["bicgstab_solves"] == gi["newton_iters"]
+    shape = g.shape
+    for name, ref in (("F", to_field(o.F, shape)), ("P", to_field(o.P, shape)), ("FP", to_field(o.Fp, shape))):
+        assert relerr(g.field(name), ref) < 1e-9, name
+    assert relerr(g.field("RHO_GND"), o.rho_gnd.reshape(shape + (12,))) < 1e-9
+    g.close()
