@@ -21,6 +21,9 @@ paper's equations in their printed order:
                    Eqs. 1-9 and Piola) and its consistent tangent.
 * ``solver``       one load increment: Nye/GND, hardening, Newton-CG on
                    Eq. linequil2ast, commit of the internal variables.
+* ``sensitivity``  forward-mode derivatives of the macroscopic stress curve
+                   with respect to (tau0, K, alpha, b) through the same
+                   increment equations, pinned by finite differences.
 
 Where the paper is silent, ambiguous or garbled the reading taken is stated
 next to the code.  Functions without an independent pin say so.
