@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                     help="replay chunks of CG iterations as captured CUDA graphs")
+    ap.add_argument("--sensitivity", action="store_true",
+                    help="time the increments with and without d<P>/d(tau0, K, alpha, b) and report the ratio")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(rvegen.WORKLOADS) + ["sweep"],
@@ -177,6 +179,18 @@ def roofline(stats, shape, peaks, local=None):
     return dom, out
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# kernels that lead the timed region, from one ncu capture of the 64^3
+# workload; keyed by (category, precision).  Kernels changed since that
+# capture have no entry (reported as null), as do other grid sizes.
+TRAFFIC_64 = {
+    ("tangent_apply", 0): 207.66e6 + 5.16e6,   # K : p reads its algorithmic 207.6 MB
+    ("constitutive", 0): 97.31e6 + 51.85e6,    # k_local (same kernel in both precisions)
+    ("constitutive", 1): 97.31e6 + 51.85e6,
+    ("tangent_build", 0): 77.02e6 + 221.57e6,  # k_tangent, K written in FP64
+}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -252,6 +266,55 @@ def cpu_cores():
 
 
 # ---------------------------------------------------------------- main
+def run_sensitivity(a):
+    """Cost of the forward-mode sensitivities: the same increments timed with
+    and without d<P>/d theta (one extra linear solve per parameter and
+    increment), device-synchronised on both sides."""
+    import torch
+    import paper_1910_01946_gb300 as pkg
+    from paper_1910_01946_gb300 import _build
+    _build.build()
+    pkg.load_library()
+    prec = 1 if a.precision == "mixed" else 0
+    wl = rvegen.WORKLOADS[a.workload]
+    gid, quat, mat = wl.inputs()
+    mask = rvegen.UNIAXIAL_X_MASK
+    out = {}
+    clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    clocks.start()
+    for sens in (False, True):
+        r = pkg.RVE(gid, quat, mat, wl.edge, own_stream=True, precision=prec, graphs=a.graphs)
+        if sens:
+            r.enable_sensitivity()
+        for _ in range(a.warmup):
+            r.step(wl.dFbar(), mask, np.zeros(9), wl.dt)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(r.stream)
+        cg = 0
+        for _ in range(a.steps):
+            cg += r.step(wl.dFbar(), mask, np.zeros(9), wl.dt)["cg_iters_total"]
+        ev1.record(r.stream)
+        torch.cuda.synchronize()
+        out[sens] = (ev0.elapsed_time(ev1) / a.steps, cg / a.steps,
+                     r.stress_sensitivity()[:, 0, 0].tolist() if sens else None)
+        r.close()
+    clocks.stop()
+    line = {"metric": "sensitivity cost: increment with d<P>/d(tau0, K, alpha, b) / increment alone",
+            "value": out[True][0] / out[False][0], "unit": "x", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": out[True][0], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == 0 else "f64 local update and residual, f32 conjugate gradients",
+            "data": "synthetic",
+            "config": {"workload": f"{wl.name}: {wl.n}^3 voxels, {wl.n_grains} grains, {wl.material}, "
+                                   f"tension {wl.strain:.0%} in {wl.increments} increments, sensitivities to "
+                                   "(tau0, K, alpha, b)", "voxels": wl.n ** 3},
+            "clocks": clocks.summary(),
+            "detail": {"ms_per_increment_forward": out[False][0], "ms_per_increment_with_sensitivities": out[True][0],
+                       "newton_cg_iters_per_increment": out[False][1],
+                       "dP11_dtheta_last_increment": out[True][2]}}
+    print(json.dumps(line))
+
+
 def run_sweep(a):
     """The batched grain-size sweep: 16 RVEs (32^3 .. 96^3, 8 .. 400 grains,
     Cu/Al/Ag/Ni) advanced together, each on its own stream.  Throughput is
@@ -319,6 +382,8 @@ def main():
     a = parse()
     if a.workload == "sweep":
         return run_sweep(a)
+    if a.sensitivity:
+        return run_sensitivity(a)
     wl = rvegen.WORKLOADS[a.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -461,7 +526,9 @@ def main():
     roof_line = None
     if roof is not None and "bound" in roof:
         roof_line = {"bound": roof["bound"], "achieved": roof["achieved"], "peak": roof["peak"], "unit": roof["unit"],
-                     "frac": roof["frac"], "traffic": None, "kernel": dom, "launches": roof["launches"],
+                     "frac": roof["frac"],
+                     "traffic": TRAFFIC_64.get((dom, prec)) if wl.n == 64 else None,
+                     "kernel": dom, "launches": roof["launches"],
                      "avg_us": roof["avg_us"], "share_of_kernel_time": roof["share"],
                      "peak_source": "FP64: derived 152 SM x 4 flop/clk x 2070 MHz" if roof["bound"] == "alu"
                      else f"HBM: MEASURED_PEAKS.json ({peaks['source']})"}

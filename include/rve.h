@@ -263,6 +263,35 @@ rve_status rve_kernel_stats(rve_t* rve, int64_t* launches, double* ms);
 rve_status rve_project_noalloc(int n0, int n1, int n2, double L, const uint8_t strain_mask[9],
                                const double* d_X, double* d_Y, void* cuda_stream);
 
+/* Sensitivities of the macroscopic stress with respect to the material
+ * parameters theta = (tau0 [MPa], K [-], alpha [-], b [m]) (differentiation of
+ * the incremental solve; the paper fits such parameters to Hall-Petch data in
+ * Sec. 4).  Forward mode through the same discrete equations rve_step solves:
+ * the hardening (Eqs. Taylor_hard, meanfree, with the GND densities of
+ * Eqs. defA2 / mingnd scaling as 1/b), the implicit local update, the
+ * equilibrium G*(K : dF) = -G*(dP|_dF=0) with the converged increment's
+ * consistent tangent (Eq. linequil2ast; one linear solve per parameter and
+ * increment, CG with a BiCGStab retry in FP64, BiCGStab in mixed precision),
+ * and the implicit Kocks-Mecking commit (Eq. kocks).  The state tangents
+ * dFp and d rho_SSD carry the load history.
+ *
+ * rve_sensitivity_bytes: device bytes the tangents and scratch need.
+ * rve_sensitivity_enable: d_workspace is caller-owned device memory (256-byte
+ *   aligned, >= rve_sensitivity_bytes, outliving the handle); the tangents
+ *   start at zero, i.e. the current state is taken as independent of theta
+ *   (exact from the initial state).  tol: relative tolerance of the linear
+ *   solves (<= 0: rve_options.cg_tol).  From then on every rve_step also
+ *   updates the sensitivities before it commits; a failed solve fails the
+ *   step (RVE_ENOCONV_CG) with nothing committed.  rve_restore zeroes the
+ *   tangents.
+ * rve_get_stress_sensitivity: dP[9 * j + 3 * i + k] = d<P_ik> / d theta_j of
+ *   the last converged increment (host array of 36); RVE_EINVAL when there is
+ *   none. */
+#define RVE_NTHETA 4
+size_t rve_sensitivity_bytes(const rve_t* rve);
+rve_status rve_sensitivity_enable(rve_t* rve, void* d_workspace, size_t bytes, double tol);
+rve_status rve_get_stress_sensitivity(rve_t* rve, double dP[RVE_NTHETA * 9]);
+
 const char* rve_last_error(const rve_t* rve);
 void rve_destroy(rve_t* rve);
 

@@ -78,6 +78,9 @@ _SIGS = {
     "rve_kernel_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "rve_project_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p]),
+    "rve_sensitivity_bytes": (C.c_size_t, [C.c_void_p]),
+    "rve_sensitivity_enable": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_double]),
+    "rve_get_stress_sensitivity": (C.c_int, [C.c_void_p, C.c_void_p]),
     "rve_last_error": (C.c_char_p, [C.c_void_p]),
     "rve_destroy": (None, [C.c_void_p]),
 }
@@ -215,6 +218,21 @@ def rve_project_noalloc(n0, n1, n2, L, mask, d_X, d_Y, stream):
                                               C.c_void_p(d_Y), C.c_void_p(stream))
 
 
+PARAMS = ("tau0", "K", "alpha", "b")   # order of the sensitivity parameters
+
+
+def rve_sensitivity_bytes(h):
+    return load_library().rve_sensitivity_bytes(h)
+
+
+def rve_sensitivity_enable(h, d_workspace, nbytes, tol=0.0):
+    return load_library().rve_sensitivity_enable(h, C.c_void_p(d_workspace), nbytes, float(tol))
+
+
+def rve_get_stress_sensitivity(h, out):
+    return load_library().rve_get_stress_sensitivity(h, _ptr(out))
+
+
 def rve_last_error(h):
     s = load_library().rve_last_error(h)
     return s.decode() if s else ""
@@ -316,6 +334,22 @@ class RVE:
         if check:
             self._check(st, "rve_step")
         return out
+
+    def enable_sensitivity(self, tol=0.0):
+        """Carry d/d(tau0, K, alpha, b) through every following increment (the
+        current state is taken as parameter-independent); workspace from torch."""
+        n = rve_sensitivity_bytes(self.h)
+        with self.torch.cuda.device(self.device):
+            self.sens_workspace = self.torch.empty(n + 256, dtype=self.torch.uint8, device=self.device)
+        base = self.sens_workspace.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        self._check(rve_sensitivity_enable(self.h, aligned, n, tol), "rve_sensitivity_enable")
+
+    def stress_sensitivity(self):
+        """d<P>/d theta of the last increment, shape (4, 3, 3), theta = PARAMS."""
+        out = np.zeros(36)
+        self._check(rve_get_stress_sensitivity(self.h, out), "rve_get_stress_sensitivity")
+        return out.reshape(4, 3, 3)
 
     def macro_stress(self):
         P, s = np.zeros(9), np.zeros(9)

@@ -100,12 +100,35 @@ __device__ __forceinline__ double blk_sum(double v, double* sh) {
   return s;
 }
 
+// Block-wide sum of a value of the field type V: the warp stage adds in V
+// (FP32 shuffles for the mixed-precision loop, where FP64 additions would
+// cost the narrow FP64 pipe), the warps' sums are added in double.  For
+// V = double it is blk_sum.
+template <typename V>
+__device__ __forceinline__ double blk_sum_v(V v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int t = lin_tid();
+  const int lane = t & 31, wid = t >> 5;
+  if (lane == 0) sh[wid] = (double)v;
+  __syncthreads();
+  double s = 0.0;
+  if (t == 0) {
+    const int nw = (lin_nthreads() + 31) >> 5;
+    for (int w = 0; w < nw; ++w) s += sh[w];
+  }
+  __syncthreads();
+  return s;
+}
+
 // After every block has written partial[c * gridDim.x + blockIdx.x] for
-// c < nval: the block that takes the last ticket sums each value over the
-// blocks in block order (deterministic) into out[c] (thread 0) and returns
-// true; every other block returns false.
+// c < nval (nval <= 9): the block that takes the last ticket sums each value
+// whose bit is set in `which` over the blocks in block order (deterministic)
+// into out[c] (thread 0; 0 for the others) and returns true; every other block
+// returns false.  The partials of all values are loaded together, so the
+// tail costs one round trip to L2 rather than one per value.
 __device__ __forceinline__ bool last_block_sums(const double* partial, int nval, unsigned int* ticket, double* sh,
-                                                double* out) {
+                                                double* out, unsigned which = 0x1FFu) {
   __shared__ bool last;
   const int t = lin_tid();
   __threadfence();
@@ -113,10 +136,19 @@ __device__ __forceinline__ bool last_block_sums(const double* partial, int nval,
   if (t == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
   __syncthreads();
   if (!last) return false;
-  for (int c = 0; c < nval; ++c) {
-    double acc = 0.0;
-    for (int i = t; i < (int)gridDim.x; i += lin_nthreads()) acc += __ldcg(partial + (size_t)c * gridDim.x + i);
-    const double s = blk_sum(acc, sh);
+  double acc[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) acc[c] = 0.0;
+  for (int i = t; i < (int)gridDim.x; i += lin_nthreads()) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c)
+      if (c < nval && ((which >> c) & 1u)) acc[c] += __ldcg(partial + (size_t)c * gridDim.x + i);
+  }
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    if (c >= nval) break;
+    double s = 0.0;
+    if ((which >> c) & 1u) s = blk_sum(acc[c], sh);
     if (t == 0) out[c] = s;
   }
   if (t == 0) *ticket = 0u;

@@ -489,6 +489,243 @@ __global__ void __launch_bounds__(128) k_tangent(
   }
 }
 
+
+// ---- forward-mode sensitivities with respect to theta = (tau0, K, alpha, b) ----
+// One parameter per launch: dth = the unit direction of that parameter.
+
+__device__ __forceinline__ double sgn(double x) { return (double)((x > 0.0) - (x < 0.0)); }
+
+// X~ = R^T X R
+__device__ __forceinline__ void to_crystal(const double* R, const double* X, double* Xt) {
+  double T[9];
+  mat3_mul(X, R, T);
+  mat3_tmul(R, T, Xt);
+}
+// X = R X~ R^T
+__device__ __forceinline__ void to_sample(const double* R, const double* Xt, double* X) {
+  double T[9];
+  mat3_mult(Xt, R, T);
+  mat3_mul(R, T, X);
+}
+
+// d tauc and d l from the Nye tensor of dFp_{k-1} (sample frame), d rho_SSD,k-1
+// and dth, at the start-of-increment state (rho18 of the increment, rho_SSD,k-1):
+//   d rho18 = A^+ dG~ - rho18 db / b  (A is proportional to b),
+//   d rho_GND^a = sgn(rho18_e^a) d rho18_e^a + 1/2 sgn(rho18_s) d rho18_s,
+//   d tauc^a = dtau0 + mu (dalpha b X^a + alpha db X^a + alpha b dX^a),
+//   X^a = sqrt(sum_b q^ab rho^b),  d l^a = dK / Y^a - K dY^a / Y^a^2,
+//   Y^a = sqrt(sum_{b != a} rho^b).
+__global__ void __launch_bounds__(128) k_hard_jvp(
+    size_t nvox, const int32_t* __restrict__ grain, const double* __restrict__ grainR,
+    const double* __restrict__ qhat, const double* __restrict__ Apinv, const int32_t* __restrict__ screw_of,
+    const double* __restrict__ dnye, const double* __restrict__ rho18, const double* __restrict__ rho_ssd,
+    const double* __restrict__ drho, double* __restrict__ dtauc, double* __restrict__ dell, Consts c, Theta dth) {
+  __shared__ double sq[144], sA[162];
+  __shared__ int sscrew[12];
+  for (int i = threadIdx.x; i < 144; i += blockDim.x) sq[i] = qhat[i];
+  for (int i = threadIdx.x; i < 162; i += blockDim.x) sA[i] = Apinv[i];
+  if (threadIdx.x < 12) sscrew[threadIdx.x] = screw_of[threadIdx.x];
+  __syncthreads();
+  const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nvox) return;
+  double R[9], G[9], Gt[9];
+  const int g = grain[v];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) R[k] = __ldg(grainR + 9 * g + k);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) G[k] = dnye[k * nvox + v];
+  to_crystal(R, G, Gt);
+  double r18[18], d18[18];
+#pragma unroll
+  for (int a = 0; a < 18; ++a) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s = fma(sA[9 * a + k], Gt[k], s);
+    r18[a] = rho18[a * nvox + v];
+    d18[a] = s - r18[a] * (dth.db / c.b);
+  }
+  double rho[12], dr[12], sum = 0.0, dsum = 0.0;
+#pragma unroll
+  for (int a = 0; a < 12; ++a) {
+    const int sa = 12 + sscrew[a];
+    double gd = 0.0, dgd = 0.0;
+    if (c.gnd_enabled) {
+      gd = fabs(r18[a]) + 0.5 * fabs(r18[sa]);
+      dgd = sgn(r18[a]) * d18[a] + 0.5 * sgn(r18[sa]) * d18[sa];
+    }
+    rho[a] = rho_ssd[a * nvox + v] + gd;
+    dr[a] = drho[a * nvox + v] + dgd;
+    sum += rho[a];
+    dsum += dr[a];
+  }
+#pragma unroll
+  for (int a = 0; a < 12; ++a) {
+    double s = 0.0, ds = 0.0;
+#pragma unroll
+    for (int b = 0; b < 12; ++b) {
+      s = fma(sq[12 * a + b], rho[b], s);
+      ds = fma(sq[12 * a + b], dr[b], ds);
+    }
+    const double X = sqrt(s), dX = ds / (2.0 * X);
+    dtauc[a * nvox + v] = dth.dtau0 + c.mu * (dth.dalpha * c.b * X + c.alpha * dth.db * X + c.alpha * c.b * dX);
+    const double Y = sqrt(sum - rho[a]), dY = (dsum - dr[a]) / (2.0 * Y);
+    dell[a * nvox + v] = dth.dK / Y - c.K * dY / (Y * Y);
+  }
+}
+
+// Directional derivative of the converged local update along (dF, dFp_{k-1},
+// dtauc), in the crystal frame (see the tangent kernel for the notation):
+//   J dS = C : sym(Fe^T dFe) with dFe = dF~ Fp^-1 + F~ dFp0inv M^-1
+//          + F~ Fp0^-1 dMinv|_tauc (the change of Fe at fixed S),
+//   d dgam^a = dgam'(tau^a) (S0^a : dS) - n dgam^a dtauc^a / tauc^a,
+//   dFp^-1 = dFp0inv M^-1 - Fp^-1 dM M^-1,
+//   dP = dF Q + F dQ, Q = Fp^-1 S Fp^-T,  dFp = dM Fp0 + M dFp0.
+// mode 0 (dF = 0): writes dP.  mode 1: writes dFp_k and d rho_SSD,k (the
+// implicit Kocks-Mecking commit differentiated) and reduces the mean of dP
+// into mean_out[9].
+__global__ void __launch_bounds__(128) k_local_jvp(
+    size_t nvox, const int32_t* __restrict__ grain, const double* __restrict__ grainR,
+    const double* __restrict__ Fin, const double* __restrict__ Fp0inv, const double* __restrict__ tauc_g,
+    const double* __restrict__ Sin, const double* __restrict__ dFin, const double* __restrict__ dFp0_g,
+    const double* __restrict__ dtauc_g, const double* __restrict__ ell_g, const double* __restrict__ dell_g,
+    const double* __restrict__ rho_g, const double* __restrict__ drho_g, double* __restrict__ dP_out,
+    double* __restrict__ dFp_out, double* __restrict__ drho_out, double* __restrict__ partial,
+    unsigned int* __restrict__ ticket, double* __restrict__ mean_out, double dt, Consts c, Theta dth, int mode) {
+  __shared__ double sh[32];
+  double acc[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc[k] = 0.0;
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (size_t)gridDim.x * blockDim.x) {
+    VoxelIn in;
+    load_voxel(nvox, v, grain, grainR, Fin, nullptr, 0.0, Fp0inv, tauc_g, in);
+    const double* R = in.R;
+    double S[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) S[k] = Sin[k * nvox + v];
+    Eval e;
+    evaluate(c, S, in.A, in.tauc, dt, e);
+    double J[36], dgp[12];
+    int piv[6];
+    jacobian(c, e, in.tauc, dt, J, dgp);
+    lu6(J, piv);
+    double X[9], dFt[9], dFp0t[9], dtc[12];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) X[k] = mode ? dFin[k * nvox + v] : 0.0;
+    to_crystal(R, X, dFt);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) X[k] = dFp0_g[k * nvox + v];
+    to_crystal(R, X, dFp0t);
+#pragma unroll
+    for (int a = 0; a < 12; ++a) dtc[a] = dtauc_g[a * nvox + v];
+    double Fpinv[9], Fe[9], FeTr[9], T1[9], T2[9], dFpi0[9], dFe[9];
+    mat3_mul(in.Fpi0, e.Minv, Fpinv);
+    mat3_mul(in.Ft, Fpinv, Fe);
+    mat3_mul(in.Ft, in.Fpi0, FeTr);
+    mat3_mul(in.Fpi0, dFp0t, T1);
+    mat3_mul(T1, in.Fpi0, dFpi0);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dFpi0[k] = -dFpi0[k];
+    // the change of M^-1 through tauc at fixed S
+    double ddg[12], dM[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < 12; ++a) {
+      ddg[a] = -c.n * e.dg[a] / in.tauc[a] * dtc[a];
+      add_schmid(dM, a, ddg[a]);
+    }
+    double dMinv[9];
+    mat3_mul(e.Minv, dM, T1);
+    mat3_mul(T1, e.Minv, dMinv);                 // negated below
+    mat3_mul(dFt, Fpinv, dFe);
+    mat3_mul(in.Ft, dFpi0, T1);
+    mat3_mul(T1, e.Minv, T2);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dFe[k] += T2[k];
+    mat3_mul(FeTr, dMinv, T2);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dFe[k] -= T2[k];
+    mat3_tmul(Fe, dFe, T1);                      // Fe^T dFe
+    double dE[6] = {T1[0], T1[4], T1[8], 0.5 * (T1[5] + T1[7]), 0.5 * (T1[2] + T1[6]), 0.5 * (T1[1] + T1[3])};
+    double dS[6];
+    cubic(c, dE, dS);
+    lu6_solve(J, piv, dS);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) dM[a] = 0.0;
+#pragma unroll
+    for (int a = 0; a < 12; ++a) {
+      ddg[a] = fma(dgp[a], resolved(dS, a), ddg[a]);
+      add_schmid(dM, a, ddg[a]);
+    }
+    // dFp^-1 = dFp0inv M^-1 - Fp^-1 dM M^-1
+    double dFpinv[9];
+    mat3_mul(dFpi0, e.Minv, dFpinv);
+    mat3_mul(Fpinv, dM, T1);
+    mat3_mul(T1, e.Minv, T2);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dFpinv[k] -= T2[k];
+    double Sf[9], dSf[9], W[9], Q[9], dQ[9];
+    sym_full(S, Sf);
+    sym_full(dS, dSf);
+    mat3_mult(Sf, Fpinv, W);                     // S Fp^-T
+    mat3_mul(Fpinv, W, Q);
+    // dQ = dFpinv S Fp^-T + Fp^-1 dS Fp^-T + (dFpinv S Fp^-T)^T
+    double A3[9];
+    mat3_mul(dFpinv, W, A3);
+    mat3_mult(dSf, Fpinv, T1);
+    mat3_mul(Fpinv, T1, T2);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) dQ[3 * i + j] = A3[3 * i + j] + A3[3 * j + i] + T2[3 * i + j];
+    double dPt[9];
+    mat3_mul(dFt, Q, dPt);
+    mat3_mul(in.Ft, dQ, T1);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dPt[k] += T1[k];
+    double dP[9];
+    to_sample(R, dPt, dP);
+    if (mode == 0) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) dP_out[k * nvox + v] = dP[k];
+      continue;
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] += dP[k];
+    // dFp = dM Fp0 + M dFp0 (crystal frame), M = I + sum dgam S0
+    double Fp0[9], Mm[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, dFpt[9];
+    mat3_inv(in.Fpi0, Fp0);
+#pragma unroll
+    for (int a = 0; a < 12; ++a) add_schmid(Mm, a, e.dg[a]);
+    mat3_mul(dM, Fp0, dFpt);
+    mat3_mul(Mm, dFp0t, T1);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dFpt[k] += T1[k];
+    to_sample(R, dFpt, X);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dFp_out[k * nvox + v] = X[k];
+    // rho_k = (rho + a / (b l)) / D, D = 1 + 2 yc a / b, a = |dgam|
+#pragma unroll
+    for (int a = 0; a < 12; ++a) {
+      const double ag = fabs(e.dg[a]), da = sgn(e.dg[a]) * ddg[a];
+      const double l = ell_g[a * nvox + v], dl = dell_g[a * nvox + v];
+      const double bl = c.b * l;
+      const double D = 1.0 + 2.0 * c.yc * ag / c.b;
+      const double dD = 2.0 * c.yc * (da / c.b - ag * dth.db / (c.b * c.b));
+      const double rk = (rho_g[a * nvox + v] + ag / bl) / D;
+      const double dnum = drho_g[a * nvox + v] + da / bl - ag * (dth.db * l + c.b * dl) / (bl * bl);
+      drho_out[a * nvox + v] = (dnum - rk * dD) / D;
+    }
+  }
+  if (mode == 0) return;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const double s = blk_sum(acc[k], sh);
+    if (threadIdx.x == 0) partial[(size_t)k * gridDim.x + blockIdx.x] = s;
+  }
+  double tot[9];
+  if (last_block_sums(partial, 9, ticket, sh, tot) && threadIdx.x == 0)
+    for (int k = 0; k < 9; ++k) mean_out[k] = tot[k] / (double)nvox;
+}
+
 }  // namespace
 
 cudaError_t launch_hardening(const rve_s* h, cudaStream_t s) {
@@ -526,4 +763,30 @@ cudaError_t launch_constitutive(const rve_s* h, double dt, double lambda, int ou
                                 cudaStream_t s) {
   if (cudaError_t e = launch_local(h, dt, lambda, out_buf, warm_buf, s)) return e;
   return launch_tangent(h, dt, lambda, out_buf, s);
+}
+
+constexpr int JVP_BLOCKS = 4 * 152;
+
+cudaError_t launch_hard_jvp(const rve_s* h, const double* dnye, const double* drho, double* dtauc, double* dell,
+                            Theta dth, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((h->nvox + 127) / 128);
+  {
+    ProfScope ps_(h, RVE_K_HARDENING, s);
+    k_hard_jvp<<<blocks, 128, 0, s>>>(h->nvox, h->grain, h->grainR, h->qhat, h->Apinv, h->screw_of, dnye, h->rho18,
+                                      h->rho_ssd, drho, dtauc, dell, h->cst, dth);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_local_jvp(const rve_s* h, double dt, int mode, const double* dF, const double* dFp0,
+                             const double* dtauc, const double* dell, const double* drho, double* dP,
+                             double* dFp_out, double* drho_out, double* mean_out, Theta dth, cudaStream_t s) {
+  {
+    ProfScope ps_(h, RVE_K_CONSTITUTIVE, s);
+    k_local_jvp<<<JVP_BLOCKS, 128, 0, s>>>(h->nvox, h->grain, h->grainR, h->F, h->Fp0inv, h->tauc, h->S[h->cur], dF,
+                                           dFp0, dtauc, h->ell, dell, h->rho_ssd, drho, dP, dFp_out, drho_out,
+                                           h->partial, (unsigned int*)(h->dcount + 4), mean_out, dt, h->cst, dth,
+                                           mode);
+  }
+  return cudaGetLastError();
 }

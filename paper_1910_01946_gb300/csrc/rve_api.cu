@@ -513,6 +513,42 @@ rve_status bicgstab_solve(rve_s* h, const uint8_t* mask, double eta, int* iters,
   return RVE_OK;
 }
 
+rve_status fail(rve_s* h, rve_status s, const char* msg);
+
+// Forward-mode sensitivities of the converged increment (before its commit):
+// for each parameter direction, the Nye tensor of dFp_{k-1} (9-field Fourier
+// curl), d tauc and d l, the local update's derivative at dF = 0, the
+// equilibrium solve G*(K : dF) = -G*(dP|_dF=0) with the converged tangent, and
+// the local derivative along dF, which also gives dFp_k, d rho_SSD,k and
+// d<P>.  The new state tangents go to the other buffer (swapped at commit).
+rve_status sens_update(rve_s* h, const uint8_t* mask, double dt) {
+  const int cur = h->cur, sc = h->sens_cur, sn = 1 - h->sens_cur;
+  RVE_CUDA(h, launch_tangent(h, dt, 0.0, cur, h->stream));
+  SpecParams curl = project_params(h, (const uint8_t*)"\0\0\0\0\0\0\0\0\0", nullptr, nullptr);
+  curl.op = OP_CURL;
+  const double eta = h->sens_tol > 0 ? h->sens_tol : h->opt.cg_tol;
+  for (int j = 0; j < RVE_NTHETA; ++j) {
+    Theta th{j == 0 ? 1.0 : 0.0, j == 1 ? 1.0 : 0.0, j == 2 ? 1.0 : 0.0, j == 3 ? 1.0 : 0.0};
+    RVE_TRY(run_project(h, h->sd_Fp[sc][j], h->s_dnye, curl));
+    RVE_CUDA(h, launch_hard_jvp(h, h->s_dnye, h->sd_rho[sc][j], h->s_dtauc, h->s_dell, th, h->stream));
+    RVE_CUDA(h, launch_local_jvp(h, dt, 0, nullptr, h->sd_Fp[sc][j], h->s_dtauc, h->s_dell, h->sd_rho[sc][j],
+                                 h->s_dP, nullptr, nullptr, nullptr, th, h->stream));
+    RVE_TRY(run_project_stencil(h, h->s_dP, h->R, mask, nullptr));
+    int it = 0;
+    bool ok = false;
+    if (h->opt.precision == 0 && h->opt.krylov != 1) RVE_TRY(cg_solve(h, mask, eta, &it, &ok));
+    if (!ok) RVE_TRY(bicgstab_solve(h, mask, std::fmax(eta, 1e-12), &it, &ok));
+    if (!ok) return fail(h, RVE_ENOCONV_CG, "the sensitivity solve did not converge");
+    RVE_CUDA(h, launch_local_jvp(h, dt, 1, h->x, h->sd_Fp[sc][j], h->s_dtauc, h->s_dell, h->sd_rho[sc][j],
+                                 nullptr, h->sd_Fp[sn][j], h->sd_rho[sn][j], h->s_mean + 9 * j, th, h->stream));
+  }
+  RVE_CUDA(h, cudaMemcpyAsync(h->sens_dP, h->s_mean, sizeof(h->sens_dP), cudaMemcpyDeviceToHost, h->stream));
+  RVE_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (double v : h->sens_dP)
+    if (!std::isfinite(v)) return fail(h, RVE_ENAN, "non-finite stress sensitivity");
+  return RVE_OK;
+}
+
 // The tangent of the evaluation that ended the last increment, built on
 // request (rve_step skips it): same F, S, frozen hardening and step.
 rve_status build_stale_tangent(rve_s* h) {
@@ -906,6 +942,11 @@ rve_status rve_step(rve_t* h, const double dFbar[9], const uint8_t strain_mask[9
     if (loc.newton_iters <= RVE_MAX_NEWTON_LOG) loc.residuals[loc.newton_iters] = res;
   }
   loc.converged = 1;
+  if (h->sens_on) {
+    h->sens_valid = 0;
+    st = sens_update(h, mask, dt);
+    if (st != RVE_OK) return finish(st);      // nothing committed
+  }
   if (cudaError_t e = launch_commit(h, h->stream)) {
     h->err = cudaGetErrorString(e);
     return finish(RVE_ECUDA);
@@ -923,7 +964,11 @@ rve_status rve_step(rve_t* h, const double dFbar[9], const uint8_t strain_mask[9
   }
   h->dt_prev = dt;
   ++h->increment;
-  h->K_stale = true;
+  h->K_stale = !h->sens_on;                   // sens_update built the converged tangent
+  if (h->sens_on) {
+    h->sens_cur = 1 - h->sens_cur;
+    h->sens_valid = 1;
+  }
   return finish(RVE_OK);
 }
 
@@ -1113,9 +1158,55 @@ rve_status rve_restore(rve_t* h, const void* host_buf, size_t bytes) {
   RVE_CUDA(h, cudaStreamSynchronize(h->stream));
   h->cur = 0;
   h->K_stale = false;
+  if (h->sens_on) {                           // the restored state is taken as parameter-independent
+    for (int j = 0; j < RVE_NTHETA; ++j) {
+      RVE_CUDA(h, cudaMemsetAsync(h->sd_Fp[h->sens_cur][j], 0, 9 * h->nvox * sizeof(double), h->stream));
+      RVE_CUDA(h, cudaMemsetAsync(h->sd_rho[h->sens_cur][j], 0, 12 * h->nvox * sizeof(double), h->stream));
+    }
+    RVE_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->sens_valid = 0;
+  }
   h->increment = hd.increment;
   h->dt_prev = hd.dt_prev;
   for (int c = 0; c < 9; ++c) { h->dFbar_prev[c] = hd.dFbar_prev[c]; h->Pmacro[c] = hd.Pmacro[c]; h->Smacro[c] = hd.Smacro[c]; }
+  return RVE_OK;
+}
+
+size_t rve_sensitivity_bytes(const rve_t* h) {
+  if (!h) return 0;
+  return (2 * RVE_NTHETA * (9 + 12) + 9 + 12 + 12 + 9) * align256(h->nvox * sizeof(double)) + 256 +
+         align256(RVE_NTHETA * 9 * sizeof(double));
+}
+
+rve_status rve_sensitivity_enable(rve_t* h, void* d_workspace, size_t bytes, double tol) {
+  if (!h || !d_workspace || bytes < rve_sensitivity_bytes(h) || (reinterpret_cast<uintptr_t>(d_workspace) & 255))
+    return RVE_EINVAL;
+  Carver c{static_cast<char*>(d_workspace)};
+  const size_t nv = h->nvox;
+  for (int b = 0; b < 2; ++b)
+    for (int j = 0; j < RVE_NTHETA; ++j) {
+      h->sd_Fp[b][j] = c.take<double>(9 * nv);
+      h->sd_rho[b][j] = c.take<double>(12 * nv);
+    }
+  h->s_dnye = c.take<double>(9 * nv);
+  h->s_dtauc = c.take<double>(12 * nv);
+  h->s_dell = c.take<double>(12 * nv);
+  h->s_dP = c.take<double>(9 * nv);
+  h->s_mean = c.take<double>(RVE_NTHETA * 9);
+  if (c.off > bytes) return fail(h, RVE_EINVAL, "sensitivity workspace too small");
+  RVE_CUDA(h, cudaMemsetAsync(d_workspace, 0, c.off, h->stream));
+  RVE_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->sens_on = true;
+  h->sens_cur = 0;
+  h->sens_tol = tol;
+  h->sens_valid = 0;
+  return RVE_OK;
+}
+
+rve_status rve_get_stress_sensitivity(rve_t* h, double dP[RVE_NTHETA * 9]) {
+  if (!h || !dP) return RVE_EINVAL;
+  if (!h->sens_on || !h->sens_valid) return fail(h, RVE_EINVAL, "no sensitivity of a converged increment");
+  for (int k = 0; k < RVE_NTHETA * 9; ++k) dP[k] = h->sens_dP[k];
   return RVE_OK;
 }
 

@@ -46,6 +46,12 @@ struct AxisTables {
   const float2* tw32;   // the twiddles rounded to float (mixed precision)
 };
 
+// Unit direction in the material parameters (tau0, K, alpha, b) of one
+// sensitivity
+struct Theta {
+  double dtau0, dK, dalpha, db;
+};
+
 struct Consts {        // material constants read by the hardening and constitutive kernels
   double C11, C12, C44, mu, b, tau0, alpha, gdot0, n, K, yc;
   int n_int;            // n if it is a positive integer <= 64, else 0 (use pow)
@@ -117,6 +123,17 @@ struct rve_s {
   bool K_stale = false;   // the converged evaluation's tangent is not built yet (built on request)
   CgGraph graphs[RVE_CG_GRAPHS];
   int graph_next = 0;
+  // forward-mode sensitivities (rve_sensitivity_enable): state tangents
+  // dFp (9) and d rho_SSD (12) per parameter, double-buffered so that a
+  // failed increment leaves them untouched; scratch fields; d<P>/d theta of
+  // the last increment
+  bool sens_on = false;
+  int sens_cur = 0;
+  double sens_tol = 0.0;
+  double *sd_Fp[2][RVE_NTHETA], *sd_rho[2][RVE_NTHETA];
+  double *s_dnye, *s_dtauc, *s_dell, *s_dP, *s_mean;
+  double sens_dP[RVE_NTHETA * 9];
+  int sens_valid = 0;
   double *R, *x, *r, *p, *t, *q;
   double *bv, *bs;      // BiCGStab vectors v and s
   double2* spec;        // 9 * nspec
@@ -183,6 +200,15 @@ cudaError_t launch_hardening(const rve_s* h, cudaStream_t s);
 cudaError_t launch_local(const rve_s* h, double dt, double lambda, int out_buf, int warm_buf, cudaStream_t s);
 // consistent tangent K[buf] at F + lambda x and the converged S[buf]
 cudaError_t launch_tangent(const rve_s* h, double dt, double lambda, int buf, cudaStream_t s);
+// sensitivities (one parameter direction per launch): d tauc, d l from the
+// Nye tensor of dFp_{k-1} and d rho_SSD,k-1; the directional derivative of
+// the converged local update (mode 0: dP at dF = 0; mode 1: dFp_k,
+// d rho_SSD,k and the mean of dP into mean_out[9])
+cudaError_t launch_hard_jvp(const rve_s* h, const double* dnye, const double* drho, double* dtauc, double* dell,
+                            Theta dth, cudaStream_t s);
+cudaError_t launch_local_jvp(const rve_s* h, double dt, int mode, const double* dF, const double* dFp0,
+                             const double* dtauc, const double* dell, const double* drho, double* dP,
+                             double* dFp_out, double* drho_out, double* mean_out, Theta dth, cudaStream_t s);
 // both
 cudaError_t launch_constitutive(const rve_s* h, double dt, double lambda, int out_buf, int warm_buf,
                                 cudaStream_t s);

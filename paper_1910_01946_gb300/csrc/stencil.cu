@@ -126,11 +126,11 @@ __global__ void __launch_bounds__(NT) k_div(Grid3 g, Tiling T, const V* __restri
       if (tx == 0 && ty == 0) partial[(size_t)c * gridDim.x + blockIdx.x] = 0.0;
       continue;
     }
-    const double s = blk_sum((double)mean[c], sh);
+    const double s = blk_sum_v<V>(mean[c], sh);
     if (tx == 0 && ty == 0) partial[(size_t)c * gridDim.x + blockIdx.x] = s;
   }
   double tot[9];
-  if (last_block_sums(partial, 9, ticket, sh, tot) && tx == 0 && ty == 0) {
+  if (last_block_sums(partial, 9, ticket, sh, tot, mean_mask) && tx == 0 && ty == 0) {
     for (int c = 0; c < 9; ++c) ds[DS_XMEAN + c] = tot[c] / (double)g.nvox;
   }
 }
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(NT) k_grad_t(Grid3 g, Tiling T, const V* __res
     }
     __syncthreads();
   }
-  const double s = blk_sum((double)acc, sh);
+  const double s = blk_sum_v<V>(acc, sh);
   if (tx == 0 && ty == 0) partial[blockIdx.x] = s;
   double tot;
   if (last_block_sums(partial, 1, ticket, sh, &tot) && tx == 0 && ty == 0) {
@@ -318,6 +318,8 @@ cudaError_t launch_grad_cg(const rve_s* h, const double* u, const uint8_t* mask,
 }
 
 cudaError_t launch_div32(const rve_s* h, const float* X, float* d, unsigned mean_mask, cudaStream_t s) {
+  // the same capped grid as in FP64: one tile per block (2048 blocks at 64^3)
+  // measured slower (41.5 against 34.6 us) than a few tiles per block
   Tiling T = tiling_of(h);
   if ((T.tx + 1) * (T.ty + 1) > SMAX) return cudaErrorInvalidValue;   // n0 odd: not a valid grid
   if (T.nblocks > DIV_BLOCKS) T.nblocks = DIV_BLOCKS;

@@ -115,8 +115,8 @@ __global__ void __launch_bounds__(RVE_RED_THREADS) k_cg_update(size_t n, double*
   }
 }
 
-// Mixed precision: the same CG step with FP32 tangent and vectors (block and
-// grid sums in FP64).  p = r (first) or r + beta p; t = K : p; alpha = rr / p.t
+// Mixed precision: the same CG step with FP32 tangent and vectors (warp sums
+// in FP32, block and grid sums in FP64).  p = r (first) or r + beta p; t = K : p; alpha = rr / p.t
 __global__ void __launch_bounds__(RVE_RED_THREADS) k_tangent_apply32(size_t nvox, const float* __restrict__ K,
                                                                      const float* __restrict__ r, float* __restrict__ p,
                                                                      float* __restrict__ t, double* __restrict__ ds,
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(RVE_RED_THREADS) k_tangent_apply32(size_t nvox
       acc = fmaf(pv[i], sacc, acc);
     }
   }
-  const double s = block_sum((double)acc, sh);
+  const double s = blk_sum_v<float>(acc, sh);   // warp stage in FP32
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
   const double tot = last_block_sum(partial, ticket, sh);
   if (threadIdx.x == 0 && !isnan(tot)) {

@@ -172,6 +172,8 @@ WORKLOADS = {
     "cu16": Workload("cu16_8g_1pct_20inc", 16, 8, "Cu", 0.01, 20, seed=1000),
     "cu64": Workload("cu64_100g_5pct_50inc", 64, 100, "Cu", 0.05, 50, seed=1001),
     "al128": Workload("al128_500g_3pct_30inc", 128, 500, "Al", 0.03, 30, seed=1002),
+    # the calibration workload: stress curve and its sensitivities to (tau0, K, alpha, b)
+    "cu64g64": Workload("cu64_64g_2pct_20inc", 64, 64, "Cu", 0.02, 20, seed=1004),
 }
 
 
