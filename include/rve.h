@@ -280,7 +280,7 @@ rve_status rve_project_noalloc(int n0, int n1, int n2, double L, const uint8_t s
  *   aligned, >= rve_sensitivity_bytes, outliving the handle); the tangents
  *   start at zero, i.e. the current state is taken as independent of theta
  *   (exact from the initial state).  tol: relative tolerance of the linear
- *   solves (<= 0: rve_options.cg_tol).  From then on every rve_step also
+ *   solves (<= 0: the larger of rve_options.cg_tol and 1e-9).  From then on every rve_step also
  *   updates the sensitivities before it commits; a failed solve fails the
  *   step (RVE_ENOCONV_CG) with nothing committed.  rve_restore zeroes the
  *   tangents.

@@ -121,12 +121,47 @@ __device__ __forceinline__ double blk_sum_v(V v, double* sh) {
   return s;
 }
 
+// Block-wide sums of up to nine values at once (bit c of `which` selects
+// value c): the shuffle trees of all values are interleaved and one pair of
+// barriers serves them all.  Each value is summed in the same order as
+// blk_sum_v (the same bits).  Results in out[] of linear thread 0 (0 for
+// unselected values).  sh: at least 10 * 32 doubles.
+template <typename V>
+__device__ __forceinline__ void blk_sums9(V* v, unsigned which, double* sh, double* out) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int c = 0; c < 9; ++c)
+      if ((which >> c) & 1u) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+  const int t = lin_tid();
+  const int lane = t & 31, wid = t >> 5;
+  if (lane == 0) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c)
+      if ((which >> c) & 1u) sh[32 * c + wid] = (double)v[c];
+  }
+  __syncthreads();
+  if (t < 9 && ((which >> t) & 1u)) {
+    const int nw = (lin_nthreads() + 31) >> 5;
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += sh[32 * t + w];
+    sh[288 + t] = s;
+  }
+  __syncthreads();
+  if (t == 0) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) out[c] = ((which >> c) & 1u) ? sh[288 + c] : 0.0;
+  }
+  __syncthreads();
+}
+
 // After every block has written partial[c * gridDim.x + blockIdx.x] for
 // c < nval (nval <= 9): the block that takes the last ticket sums each value
 // whose bit is set in `which` over the blocks in block order (deterministic)
 // into out[c] (thread 0; 0 for the others) and returns true; every other block
-// returns false.  The partials of all values are loaded together, so the
-// tail costs one round trip to L2 rather than one per value.
+// returns false.  The partials of all values are loaded together and summed
+// by one fused block reduction, so the tail costs one round trip to L2 rather
+// than one per value.  sh: at least 10 * 32 doubles.
 __device__ __forceinline__ bool last_block_sums(const double* partial, int nval, unsigned int* ticket, double* sh,
                                                 double* out, unsigned which = 0x1FFu) {
   __shared__ bool last;
@@ -144,13 +179,11 @@ __device__ __forceinline__ bool last_block_sums(const double* partial, int nval,
     for (int c = 0; c < 9; ++c)
       if (c < nval && ((which >> c) & 1u)) acc[c] += __ldcg(partial + (size_t)c * gridDim.x + i);
   }
-#pragma unroll
-  for (int c = 0; c < 9; ++c) {
-    if (c >= nval) break;
-    double s = 0.0;
-    if ((which >> c) & 1u) s = blk_sum(acc[c], sh);
-    if (t == 0) out[c] = s;
+  double res[9];
+  blk_sums9<double>(acc, which & ((1u << nval) - 1u), sh, res);
+  if (t == 0) {
+    for (int c = 0; c < nval; ++c) out[c] = res[c];
+    *ticket = 0u;
   }
-  if (t == 0) *ticket = 0u;
   return true;
 }

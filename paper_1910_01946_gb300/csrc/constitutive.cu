@@ -91,14 +91,16 @@ struct Eval {
   double rn;      // max |r|, +inf when rejected
 };
 
-// Evaluate the residual at S; A = FeTr^T FeTr (full 3x3, symmetric).
-__device__ void evaluate(const Consts& c, const double* S, const double* A, const double* tauc, double dt, Eval& e) {
+// Evaluate the residual at S; A = FeTr^T FeTr (full 3x3, symmetric); tinv =
+// 1 / tauc (divisions cost several FP64 instructions each: every kernel forms
+// the twelve reciprocals once per voxel and multiplies).
+__device__ void evaluate(const Consts& c, const double* S, const double* A, const double* tinv, double dt, Eval& e) {
   double M[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   bool bad = false;
 #pragma unroll
   for (int a = 0; a < 12; ++a) {
     const double t = resolved(S, a);
-    const double x = t / tauc[a];
+    const double x = t * tinv[a];
     const double ax = fabs(x);
     const double xn = c.n_int ? ipow(ax, c.n_int) : pow(ax, c.n);
     double g = dt * c.gdot0 * xn;
@@ -133,16 +135,16 @@ __device__ void evaluate(const Consts& c, const double* S, const double* A, cons
 }
 
 // J = I - sum_a c^a (x) w^a with c^a = -dgp^a C : sym(Ce S0^a Minv)
-__device__ void jacobian(const Consts& c, const Eval& e, const double* tauc, double dt, double* J, double* dgp) {
+__device__ void jacobian(const Consts& c, const Eval& e, const double* tinv, double dt, double* J, double* dgp) {
 #pragma unroll
   for (int i = 0; i < 36; ++i) J[i] = (i % 7 == 0) ? 1.0 : 0.0;
   double Cf[9];
   sym_full(e.Ce, Cf);
 #pragma unroll
   for (int a = 0; a < 12; ++a) {
-    const double x = fabs(e.tau[a] / tauc[a]);
+    const double x = fabs(e.tau[a] * tinv[a]);
     const double xn1 = c.n_int ? ipow(x, c.n_int - 1) : pow(x, c.n - 1.0);
-    const double gp = dt * c.gdot0 * c.n * xn1 / tauc[a];
+    const double gp = dt * c.gdot0 * c.n * xn1 * tinv[a];
     dgp[a] = gp;
     // u = Ce s', w = Minv^T m'  (times 1/sqrt6 folded in below)
     double u[3], w[3];
@@ -165,7 +167,8 @@ __device__ void jacobian(const Consts& c, const Eval& e, const double* tauc, dou
   }
 }
 
-// LU with partial pivoting of a 6x6 matrix in place; piv[k] = row swapped into k
+// LU with partial pivoting of a 6x6 matrix in place (the diagonal holds the
+// reciprocal pivots); piv[k] = row swapped into k
 __device__ void lu6(double* J, int* piv) {
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
@@ -184,6 +187,7 @@ __device__ void lu6(double* J, int* piv) {
       }
     }
     const double inv = 1.0 / J[6 * k + k];
+    J[6 * k + k] = inv;                 // the solves multiply by the reciprocal pivot
 #pragma unroll
     for (int i = k + 1; i < 6; ++i) {
       const double l = J[6 * i + k] * inv;
@@ -208,7 +212,7 @@ __device__ void lu6_solve(const double* LU, const int* piv, double* b) {
   for (int i = 5; i >= 0; --i) {
 #pragma unroll
     for (int j = i + 1; j < 6; ++j) b[i] = fma(-LU[6 * i + j], b[j], b[i]);
-    b[i] /= LU[6 * i + i];
+    b[i] *= LU[6 * i + i];
   }
 }
 
@@ -275,7 +279,7 @@ __global__ void __launch_bounds__(128) k_hardening(
 // trial elastic right Cauchy-Green tensor A = (F~ Fp_prev^-1)^T (F~ Fp_prev^-1)
 // and the frozen critical resolved shear stresses.
 struct VoxelIn {
-  double R[9], Ft[9], Fpi0[9], A[9], tauc[12];
+  double R[9], Ft[9], Fpi0[9], A[9], tinv[12];   // tinv = 1 / tauc
 };
 
 __device__ __forceinline__ void load_voxel(size_t nvox, size_t v, const int32_t* __restrict__ grain,
@@ -299,7 +303,7 @@ __device__ __forceinline__ void load_voxel(size_t nvox, size_t v, const int32_t*
   mat3_mul(in.Ft, in.Fpi0, FeTr);
   mat3_tmul(FeTr, FeTr, in.A);
 #pragma unroll
-  for (int a = 0; a < 12; ++a) in.tauc[a] = tauc_g[a * nvox + v];
+  for (int a = 0; a < 12; ++a) in.tinv[a] = 1.0 / tauc_g[a * nvox + v];
 }
 
 // P = Fe S Fp^-T = F~ (Fp^-1 S Fp^-T) in the crystal frame, rotated to the
@@ -328,25 +332,25 @@ __global__ void __launch_bounds__(128) k_local(
     VoxelIn in;
     load_voxel(nvox, v, grain, grainR, Fin, xdir, lambda, Fp0inv, tauc_g, in);
     const double* A = in.A;
-    const double* tauc = in.tauc;
+    const double* tinv = in.tinv;      // 1 / tauc
     double S[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) S[k] = Swarm[k * nvox + v];
 
     Eval e;
-    evaluate(c, S, A, tauc, dt, e);
+    evaluate(c, S, A, tinv, dt, e);
     ++evals;
     if (!(e.rn < INFINITY)) {             // warm start rejected: restart from the elastic-free state
 #pragma unroll
       for (int k = 0; k < 6; ++k) S[k] = 0.0;
-      evaluate(c, S, A, tauc, dt, e);
+      evaluate(c, S, A, tinv, dt, e);
       ++evals;
     }
     double J[36], dgp[12];
     int piv[6];
     bool conv = e.rn <= c.local_tol_abs;
     while (!conv && iters < c.max_local) {
-      jacobian(c, e, tauc, dt, J, dgp);
+      jacobian(c, e, tinv, dt, J, dgp);
       lu6(J, piv);
       double d[6];
 #pragma unroll
@@ -359,7 +363,7 @@ __global__ void __launch_bounds__(128) k_local(
 #pragma unroll
         for (int k = 0; k < 6; ++k) St[k] = fma(lam, d[k], S[k]);
         Eval et;
-        evaluate(c, St, A, tauc, dt, et);
+        evaluate(c, St, A, tinv, dt, et);
         ++evals;
         if (et.rn < e.rn) {
 #pragma unroll
@@ -418,15 +422,15 @@ __global__ void __launch_bounds__(128) k_tangent(
     const double* R = in.R;
     const double* Ft = in.Ft;
     const double* Fpi0 = in.Fpi0;
-    const double* tauc = in.tauc;
+    const double* tinv = in.tinv;      // 1 / tauc
     double S[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) S[k] = Sin[k * nvox + v];
     Eval e;
-    evaluate(c, S, in.A, tauc, dt, e);
+    evaluate(c, S, in.A, tinv, dt, e);
     double J[36], dgp[12];
     int piv[6];
-    jacobian(c, e, tauc, dt, J, dgp);
+    jacobian(c, e, tinv, dt, J, dgp);
     lu6(J, piv);
     double Fpinv[9], Fe[9], Sf[9], W[9], Q[9];
     mat3_mul(Fpi0, e.Minv, Fpinv);
@@ -591,7 +595,7 @@ __global__ void __launch_bounds__(128) k_local_jvp(
     const double* __restrict__ rho_g, const double* __restrict__ drho_g, double* __restrict__ dP_out,
     double* __restrict__ dFp_out, double* __restrict__ drho_out, double* __restrict__ partial,
     unsigned int* __restrict__ ticket, double* __restrict__ mean_out, double dt, Consts c, Theta dth, int mode) {
-  __shared__ double sh[32];
+  __shared__ double sh[320];
   double acc[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) acc[k] = 0.0;
@@ -603,10 +607,10 @@ __global__ void __launch_bounds__(128) k_local_jvp(
 #pragma unroll
     for (int k = 0; k < 6; ++k) S[k] = Sin[k * nvox + v];
     Eval e;
-    evaluate(c, S, in.A, in.tauc, dt, e);
+    evaluate(c, S, in.A, in.tinv, dt, e);
     double J[36], dgp[12];
     int piv[6];
-    jacobian(c, e, in.tauc, dt, J, dgp);
+    jacobian(c, e, in.tinv, dt, J, dgp);
     lu6(J, piv);
     double X[9], dFt[9], dFp0t[9], dtc[12];
 #pragma unroll
@@ -629,7 +633,7 @@ __global__ void __launch_bounds__(128) k_local_jvp(
     double ddg[12], dM[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
     for (int a = 0; a < 12; ++a) {
-      ddg[a] = -c.n * e.dg[a] / in.tauc[a] * dtc[a];
+      ddg[a] = -c.n * e.dg[a] * in.tinv[a] * dtc[a];
       add_schmid(dM, a, ddg[a]);
     }
     double dMinv[9];
@@ -716,11 +720,10 @@ __global__ void __launch_bounds__(128) k_local_jvp(
     }
   }
   if (mode == 0) return;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    const double s = blk_sum(acc[k], sh);
-    if (threadIdx.x == 0) partial[(size_t)k * gridDim.x + blockIdx.x] = s;
-  }
+  double bs[9];
+  blk_sums9<double>(acc, 0x1FFu, sh, bs);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 9; ++k) partial[(size_t)k * gridDim.x + blockIdx.x] = bs[k];
   double tot[9];
   if (last_block_sums(partial, 9, ticket, sh, tot) && threadIdx.x == 0)
     for (int k = 0; k < 9; ++k) mean_out[k] = tot[k] / (double)nvox;

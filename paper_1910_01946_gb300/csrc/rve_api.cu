@@ -526,7 +526,9 @@ rve_status sens_update(rve_s* h, const uint8_t* mask, double dt) {
   RVE_CUDA(h, launch_tangent(h, dt, 0.0, cur, h->stream));
   SpecParams curl = project_params(h, (const uint8_t*)"\0\0\0\0\0\0\0\0\0", nullptr, nullptr);
   curl.op = OP_CURL;
-  const double eta = h->sens_tol > 0 ? h->sens_tol : h->opt.cg_tol;
+  // the sensitivities need a few more digits than their uses (gradients
+  // checked to 1e-5 against differences): 1e-9 by default
+  const double eta = h->sens_tol > 0 ? h->sens_tol : std::fmax(h->opt.cg_tol, 1e-9);
   for (int j = 0; j < RVE_NTHETA; ++j) {
     Theta th{j == 0 ? 1.0 : 0.0, j == 1 ? 1.0 : 0.0, j == 2 ? 1.0 : 0.0, j == 3 ? 1.0 : 0.0};
     RVE_TRY(run_project(h, h->sd_Fp[sc][j], h->s_dnye, curl));
@@ -539,6 +541,7 @@ rve_status sens_update(rve_s* h, const uint8_t* mask, double dt) {
     if (h->opt.precision == 0 && h->opt.krylov != 1) RVE_TRY(cg_solve(h, mask, eta, &it, &ok));
     if (!ok) RVE_TRY(bicgstab_solve(h, mask, std::fmax(eta, 1e-12), &it, &ok));
     if (!ok) return fail(h, RVE_ENOCONV_CG, "the sensitivity solve did not converge");
+    RVE_CUDA(h, launch_zero_means(h, h->x, 0x1FFu & ~kept_means(mask), h->stream));
     RVE_CUDA(h, launch_local_jvp(h, dt, 1, h->x, h->sd_Fp[sc][j], h->s_dtauc, h->s_dell, h->sd_rho[sc][j],
                                  nullptr, h->sd_Fp[sn][j], h->sd_rho[sn][j], h->s_mean + 9 * j, th, h->stream));
   }
@@ -896,6 +899,10 @@ rve_status rve_step(rve_t* h, const double dFbar[9], const uint8_t strain_mask[9
         st = h->opt.precision == 1 ? cg_solve32(h, mask, eta, &ncg, &cgok) : cg_solve(h, mask, eta, &ncg, &cgok);
       }
       if (st != RVE_OK) return finish(st);
+      // dF has zero strain-controlled means by construction (every Krylov vector
+      // is a projection); remove what round-off left there, which a long or
+      // stalled solve with a large dF would otherwise carry into <F>
+      RVE_CUDA(h, launch_zero_means(h, h->x, 0x1FFu & ~kept_means(mask), h->stream));
       if (loc.newton_iters < RVE_MAX_NEWTON_LOG) loc.cg_iters[loc.newton_iters] += ncg;
       loc.cg_iters_total += ncg;
       // backtracking on phi(lam) = rms(R(F + lam dF))^2 with sufficient decrease;

@@ -223,6 +223,8 @@ cudaError_t launch_tangent_apply32(const rve_s* h, cudaStream_t s);
 cudaError_t launch_cg_init32(const rve_s* h, double eta, cudaStream_t s);
 cudaError_t launch_widen_x(const rve_s* h, cudaStream_t s);
 cudaError_t launch_widen(const rve_s* h, const float* a, double* b, size_t n, cudaStream_t s);
+// x_c -= mean(x_c) for the components whose bit is set (uses DS_XMEAN)
+cudaError_t launch_zero_means(const rve_s* h, double* x, unsigned bits, cudaStream_t s);
 cudaError_t launch_kmul(const rve_s* h, const double* in, double* out, cudaStream_t s);
 cudaError_t launch_dots(const rve_s* h, int np, const double* a0, const double* b0, const double* a1,
                         const double* b1, const double* a2, const double* b2, int slot, cudaStream_t s);

@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(NT) k_div(Grid3 g, Tiling T, const V* __restri
                                            double* __restrict__ partial, unsigned int* __restrict__ ticket,
                                            int check_done, unsigned mean_mask) {
   __shared__ V S[9][SMAX];
-  __shared__ double sh[32];
+  __shared__ double sh[320];
   if (check_done && ds[DS_DONE] != 0.0) return;
   const int W = T.tx + 1;     // row pitch of the staged tile (with its halo)
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -120,14 +120,11 @@ __global__ void __launch_bounds__(NT) k_div(Grid3 g, Tiling T, const V* __restri
     }
     __syncthreads();
   }
+  double bs[9];
+  blk_sums9<V>(mean, mean_mask, sh, bs);       // unselected means: zero partials
+  if (tx == 0 && ty == 0) {
 #pragma unroll
-  for (int c = 0; c < 9; ++c) {
-    if (!((mean_mask >> c) & 1u)) {          // not needed: a zero partial
-      if (tx == 0 && ty == 0) partial[(size_t)c * gridDim.x + blockIdx.x] = 0.0;
-      continue;
-    }
-    const double s = blk_sum_v<V>(mean[c], sh);
-    if (tx == 0 && ty == 0) partial[(size_t)c * gridDim.x + blockIdx.x] = s;
+    for (int c = 0; c < 9; ++c) partial[(size_t)c * gridDim.x + blockIdx.x] = bs[c];
   }
   double tot[9];
   if (last_block_sums(partial, 9, ticket, sh, tot, mean_mask) && tx == 0 && ty == 0) {
@@ -150,7 +147,7 @@ __global__ void __launch_bounds__(NT) k_grad_t(Grid3 g, Tiling T, const V* __res
                                               double* __restrict__ ds, double* __restrict__ partial,
                                               unsigned int* __restrict__ ticket) {
   __shared__ V SP[3][SMAX], SM[3][SMAX];
-  __shared__ double sh[32];
+  __shared__ double sh[320];
   if (CG && ds[DS_DONE] != 0.0) return;
   const V alpha = CG ? (V)ds[DS_ALPHA] : (V)0;
   V off[9];

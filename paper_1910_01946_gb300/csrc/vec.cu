@@ -9,6 +9,10 @@
 
 namespace {
 
+// k_macro and k_mean9 reduce 27 and 9 values per thread at the end (five
+// shuffle additions each, FP64): one block per SM amortises that over many voxels
+constexpr int MACRO_BLOCKS = 152;
+
 __device__ __forceinline__ double block_sum(double v, double* sh) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -47,7 +51,7 @@ __global__ void __launch_bounds__(RVE_RED_THREADS, 2) k_tangent_apply(size_t nvo
                                                                       double* __restrict__ t, double* __restrict__ ds,
                                                                       double* __restrict__ partial,
                                                                       unsigned int* __restrict__ ticket) {
-  __shared__ double sh[32];
+  __shared__ double sh[320];
   if (ds[DS_DONE] != 0.0) return;
   // the first iteration of a solve (the counter is reset by the CG init and
   // bumped by each completed iteration): every launch of the loop has the
@@ -94,7 +98,7 @@ __global__ void __launch_bounds__(RVE_RED_THREADS) k_cg_update(size_t n, double*
                                                                const double* __restrict__ p, const double* __restrict__ q,
                                                                double* __restrict__ ds, double* __restrict__ partial,
                                                                unsigned int* __restrict__ ticket) {
-  __shared__ double sh[32];
+  __shared__ double sh[320];
   if (ds[DS_DONE] != 0.0) return;
   const double alpha = ds[DS_ALPHA];
   double acc = 0.0;
@@ -117,18 +121,23 @@ __global__ void __launch_bounds__(RVE_RED_THREADS) k_cg_update(size_t n, double*
 
 // Mixed precision: the same CG step with FP32 tangent and vectors (warp sums
 // in FP32, block and grid sums in FP64).  p = r (first) or r + beta p; t = K : p; alpha = rr / p.t
-__global__ void __launch_bounds__(RVE_RED_THREADS) k_tangent_apply32(size_t nvox, const float* __restrict__ K,
+__global__ void __launch_bounds__(RVE_RED_THREADS, 2) k_tangent_apply32(size_t nvox, const float* __restrict__ K,
                                                                      const float* __restrict__ r, float* __restrict__ p,
                                                                      float* __restrict__ t, double* __restrict__ ds,
                                                                      double* __restrict__ partial,
                                                                      unsigned int* __restrict__ ticket) {
-  __shared__ double sh[32];
+  __shared__ double sh[320];
   if (ds[DS_DONE] != 0.0) return;
   const bool first = ds[DS_ITERS] == 0.0;
   const float beta = first ? 0.0f : (float)ds[DS_BETA];
   float acc = 0.0f;
   for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (size_t)gridDim.x * blockDim.x) {
-    float pv[9];
+    // all 81 tangent loads are issued before any arithmetic: in FP32 the
+    // kernel is bound by HBM, and one round trip per voxel instead of one per
+    // row keeps enough bytes in flight
+    float kk[81], pv[9];
+#pragma unroll
+    for (int e = 0; e < 81; ++e) kk[e] = __ldcs(K + (size_t)e * nvox + v);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       const float rv = r[k * nvox + v];
@@ -139,7 +148,7 @@ __global__ void __launch_bounds__(RVE_RED_THREADS) k_tangent_apply32(size_t nvox
     for (int i = 0; i < 9; ++i) {
       float sacc = 0.0f;
 #pragma unroll
-      for (int j = 0; j < 9; ++j) sacc = fmaf(__ldcs(K + (size_t)(9 * i + j) * nvox + v), pv[j], sacc);
+      for (int j = 0; j < 9; ++j) sacc = fmaf(kk[9 * i + j], pv[j], sacc);
       t[i * nvox + v] = sacc;
       acc = fmaf(pv[i], sacc, acc);
     }
@@ -158,7 +167,7 @@ __global__ void __launch_bounds__(RVE_RED_THREADS) k_cg_init32(size_t n, float* 
                                                                const double* __restrict__ R, double* __restrict__ ds,
                                                                double eta, double* __restrict__ partial,
                                                                unsigned int* __restrict__ ticket) {
-  __shared__ double sh[32];
+  __shared__ double sh[320];
   double acc = 0.0;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     x[e] = 0.0f;
@@ -187,7 +196,7 @@ __global__ void __launch_bounds__(RVE_RED_THREADS) k_cg_init(size_t n, double* _
                                                              const double* __restrict__ R, double* __restrict__ ds,
                                                              double eta, double* __restrict__ partial,
                                                              unsigned int* __restrict__ ticket) {
-  __shared__ double sh[32];
+  __shared__ double sh[320];
   double acc = 0.0;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     x[e] = 0.0;
@@ -207,7 +216,7 @@ __global__ void __launch_bounds__(RVE_RED_THREADS) k_cg_init(size_t n, double* _
 }
 
 __global__ void __launch_bounds__(RVE_RED_THREADS) k_norm2(size_t n, const double* __restrict__ a, double* __restrict__ partial) {
-  __shared__ double sh[32];
+  __shared__ double sh[320];
   double acc = 0.0;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
     acc = fma(a[e], a[e], acc);
@@ -217,7 +226,7 @@ __global__ void __launch_bounds__(RVE_RED_THREADS) k_norm2(size_t n, const doubl
 
 __global__ void __launch_bounds__(1024) k_reduce_final(const double* __restrict__ partial, int nparts, int nval,
                                                        int mode, double* __restrict__ ds) {
-  __shared__ double sh[32];
+  __shared__ double sh[320];
   for (int c = 0; c < nval; ++c) {
     double acc = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += partial[(size_t)c * nparts + i];
@@ -317,7 +326,7 @@ __device__ __forceinline__ void cauchy(const double* P, const double* F, double*
 // partial sums of P, sigma, F (27 values) over the committed state
 __global__ void __launch_bounds__(RVE_RED_THREADS) k_macro(size_t nvox, const double* __restrict__ P,
                                                            const double* __restrict__ F, double* __restrict__ partial) {
-  __shared__ double sh[32];
+  __shared__ double sh[320];
   double acc[27];
 #pragma unroll
   for (int c = 0; c < 27; ++c) acc[c] = 0.0;
@@ -329,9 +338,11 @@ __global__ void __launch_bounds__(RVE_RED_THREADS) k_macro(size_t nvox, const do
 #pragma unroll
     for (int k = 0; k < 9; ++k) { acc[k] += Pv[k]; acc[9 + k] += sg[k]; acc[18 + k] += Fv[k]; }
   }
-  for (int c = 0; c < 27; ++c) {
-    const double s = block_sum(acc[c], sh);
-    if (threadIdx.x == 0) partial[(size_t)c * gridDim.x + blockIdx.x] = s;
+  for (int g = 0; g < 3; ++g) {
+    double bs[9];
+    blk_sums9<double>(acc + 9 * g, 0x1FFu, sh, bs);
+    if (threadIdx.x == 0)
+      for (int c = 0; c < 9; ++c) partial[(size_t)(9 * g + c) * gridDim.x + blockIdx.x] = bs[c];
   }
 }
 
@@ -422,10 +433,6 @@ cudaError_t launch_norm2(const rve_s* h, const double* a, int ncomp, cudaStream_
   if (e != cudaSuccess) return e;
   return launch_reduce_final(h, RED_NORM, s);
 }
-
-// k_macro reduces 27 values per thread at the end (five shuffle additions
-// each, FP64): one block per SM amortises that over many voxels
-constexpr int MACRO_BLOCKS = 152;
 
 cudaError_t launch_reduce_final(const rve_s* h, int mode, cudaStream_t s) {
   const int nval = mode == RED_MACRO ? 27 : 1;
@@ -547,7 +554,7 @@ __global__ void __launch_bounds__(RVE_RED_THREADS) k_dots(size_t n, int np, cons
                                                           const double* __restrict__ b2, double* __restrict__ ds,
                                                           int slot, double* __restrict__ partial,
                                                           unsigned int* __restrict__ ticket) {
-  __shared__ double sh[32];
+  __shared__ double sh[320];
   double acc[3] = {0.0, 0.0, 0.0};
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     acc[0] = fma(a0[e], b0[e], acc[0]);
@@ -574,7 +581,53 @@ __global__ void k_lincomb(size_t n, double* out, double c0, const double* a0, do
   }
 }
 
+// Means of the nine components of a field -> ds[slot + c] (last-block sum).
+__global__ void __launch_bounds__(RVE_RED_THREADS) k_mean9(size_t nvox, const double* __restrict__ x,
+                                                          double* __restrict__ ds, int slot,
+                                                          double* __restrict__ partial,
+                                                          unsigned int* __restrict__ ticket) {
+  __shared__ double sh[320];
+  double acc[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) acc[c] = 0.0;
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) acc[c] += x[c * nvox + v];
+  }
+  double bs[9];
+  blk_sums9<double>(acc, 0x1FFu, sh, bs);
+  if (threadIdx.x == 0)
+    for (int c = 0; c < 9; ++c) partial[(size_t)c * gridDim.x + blockIdx.x] = bs[c];
+  double tot[9];
+  if (last_block_sums(partial, 9, ticket, sh, tot) && threadIdx.x == 0)
+    for (int c = 0; c < 9; ++c) ds[slot + c] = tot[c] / (double)nvox;
+}
+
+// x_c -= mean(x_c) on the components whose bit is set
+__global__ void k_sub_means(size_t nvox, double* __restrict__ x, const double* __restrict__ ds, int slot,
+                            unsigned bits) {
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c)
+      if ((bits >> c) & 1u) x[c * nvox + v] -= ds[slot + c];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_zero_means(const rve_s* h, double* x, unsigned bits, cudaStream_t s) {
+  {
+    ProfScope ps_(h, RVE_K_REDUCE, s);
+    k_mean9<<<MACRO_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, x, h->dscal, DS_XMEAN, h->partial,
+                                                       (unsigned int*)(h->dcount + 4));
+  }
+  if (cudaError_t e = cudaGetLastError()) return e;
+  {
+    ProfScope ps_(h, RVE_K_OTHER, s);
+    k_sub_means<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, x, h->dscal, DS_XMEAN, bits);
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_kmul(const rve_s* h, const double* in, double* out, cudaStream_t s) {
   {
