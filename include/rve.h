@@ -94,6 +94,8 @@ typedef struct {
   int32_t graphs;        /* nonzero: chunks of 8 CG iterations are captured once into a CUDA graph
                             and replayed with one launch (needs a stream other than the legacy
                             default stream; ignored there).  Results are bit-identical. */
+  int32_t tma;           /* nonzero: the FP32 tangent apply streams the tangent through shared
+                            memory with bulk asynchronous copies (precision 1 only) */
 } rve_options;
 
 #define RVE_MAX_NEWTON_LOG 64

@@ -45,7 +45,7 @@ class rve_options(C.Structure):
                 ("local_tol", C.c_double), ("max_newton", C.c_int32), ("max_cg", C.c_int32),
                 ("max_local", C.c_int32), ("max_halvings", C.c_int32), ("extrapolate", C.c_int32),
                 ("precision", C.c_int32), ("cg_adaptive", C.c_int32), ("krylov", C.c_int32),
-                ("graphs", C.c_int32)]
+                ("graphs", C.c_int32), ("tma", C.c_int32)]
 
 
 class rve_step_info(C.Structure):
@@ -244,7 +244,7 @@ def rve_destroy(h):
 
 # ---- handle wrapper ---------------------------------------------------------
 DEFAULT_OPTIONS = dict(newton_tol=1e-11, cg_tol=1e-11, local_tol=1e-14, max_newton=100, max_cg=2000,
-                       max_local=60, max_halvings=12, extrapolate=1, precision=0, cg_adaptive=1, krylov=0, graphs=1)
+                       max_local=60, max_halvings=12, extrapolate=1, precision=0, cg_adaptive=1, krylov=0, graphs=1, tma=1)
 
 
 def make_material(m) -> rve_material:

@@ -35,6 +35,8 @@ const uint32_t CKPT_VERSION = 1;
     if (s_ != RVE_OK) return s_;        \
   } while (0)
 
+rve_status fail(rve_s* h, rve_status s, const char* msg);
+
 bool good_len(int n, int lo) {
   if (n < lo || n > 512) return false;
   FFTPlan p;
@@ -436,6 +438,7 @@ rve_status cg_solve32(rve_s* h, const uint8_t* mask, double eta, int* iters, boo
     RVE_TRY(chunk == CG_CHUNK ? cg_chunk(h, mask, issue) : issue());
     issued += chunk;
     RVE_TRY(read_scalars(h));
+    if (h->hscal[DS_ERR] != 0.0) return fail(h, RVE_ECUDA, "a bounded wait for a staged copy gave up");
     if (h->hscal[DS_DONE] != 0.0) break;
   }
   RVE_CUDA(h, launch_widen_x(h, h->stream));
@@ -512,8 +515,6 @@ rve_status bicgstab_solve(rve_s* h, const uint8_t* mask, double eta, int* iters,
   *iters = k;
   return RVE_OK;
 }
-
-rve_status fail(rve_s* h, rve_status s, const char* msg);
 
 // Forward-mode sensitivities of the converged increment (before its commit):
 // for each parameter direction, the Nye tensor of dFp_{k-1} (9-field Fourier
@@ -699,6 +700,9 @@ rve_status rve_create(const int32_t* grain_id, int n0, int n1, int n2, const dou
   h->stream = (cudaStream_t)cuda_stream;
   h->device = 0;
   cudaGetDevice(&h->device);
+  if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || h->num_sms < 1)
+    h->num_sms = 152;
+  h->tma_apply = opt->tma != 0 && opt->precision == 1 && vec_init() == cudaSuccess;
   h->h = opt->L / n0;
   h->mu = mat->mu > 0 ? mat->mu : 3.0 * mat->C44 * (mat->C11 - mat->C12) / (4.0 * mat->C44 + mat->C11 - mat->C12);
   h->cur = 0;

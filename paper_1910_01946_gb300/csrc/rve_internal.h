@@ -123,6 +123,8 @@ struct rve_s {
   bool K_stale = false;   // the converged evaluation's tangent is not built yet (built on request)
   CgGraph graphs[RVE_CG_GRAPHS];
   int graph_next = 0;
+  int num_sms = 152;        // of the handle's device
+  bool tma_apply = false;   // FP32 tangent apply staged by bulk copies (rve_options.tma)
   // forward-mode sensitivities (rve_sensitivity_enable): state tangents
   // dFp (9) and d rho_SSD (12) per parameter, double-buffered so that a
   // failed increment leaves them untouched; scratch fields; d<P>/d theta of
@@ -165,7 +167,9 @@ struct ProfScope {
 // device scalar slots
 enum { DS_RR = 0, DS_PKP = 1, DS_ALPHA = 2, DS_BETA = 3, DS_NORM = 4, DS_STOP = 5, DS_DONE = 6, DS_ITERS = 7,
        DS_MEANP = 8,
-       DS_MEANSIG = 17, DS_MEANF = 26, DS_DOT = 35, DS_XMEAN = 48 };
+       DS_MEANSIG = 17, DS_MEANF = 26, DS_DOT = 35,
+       DS_ERR = 40,      // nonzero: a kernel gave up a bounded wait (sticky)
+       DS_XMEAN = 48 };
 
 // ---- fft.cu ----
 // `done` (nullable, device): when *done != 0 every block returns at once (the
@@ -220,6 +224,8 @@ cudaError_t launch_norm2(const rve_s* h, const double* a, int ncomp, cudaStream_
 cudaError_t launch_reduce_final(const rve_s* h, int mode, cudaStream_t s);
 cudaError_t launch_cg_init(const rve_s* h, double eta, cudaStream_t s);
 cudaError_t launch_tangent_apply32(const rve_s* h, cudaStream_t s);
+// one-time kernel attributes (shared-memory sizes); before any launch or capture
+cudaError_t vec_init();
 cudaError_t launch_cg_init32(const rve_s* h, double eta, cudaStream_t s);
 cudaError_t launch_widen_x(const rve_s* h, cudaStream_t s);
 cudaError_t launch_widen(const rve_s* h, const float* a, double* b, size_t n, cudaStream_t s);

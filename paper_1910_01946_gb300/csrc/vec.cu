@@ -162,6 +162,140 @@ __global__ void __launch_bounds__(RVE_RED_THREADS, 2) k_tangent_apply32(size_t n
   }
 }
 
+// ---- TMA-staged FP32 tangent apply ----
+// The FP32 CG step is bound by HBM: 324 of its 396 bytes per voxel are the
+// tangent.  A persistent block per SM streams 256-voxel tiles of the 81
+// tangent rows and of r and p (99 rows) into shared memory with bulk
+// asynchronous copies (one 1 KB copy per row, completion counted on an
+// mbarrier), double-buffered, so the copy engine keeps the bytes in flight
+// instead of per-thread loads.
+constexpr int TA_TV = 256;                       // voxels per tile = threads per block
+constexpr int TA_ROWS = 81 + 9 + 9;              // K, r, p
+constexpr int TA_STAGE = TA_ROWS * TA_TV;        // floats per stage
+constexpr unsigned TA_STAGE_BYTES = TA_STAGE * sizeof(float);
+constexpr size_t TA_SMEM = 2 * (size_t)TA_STAGE_BYTES + 64;
+constexpr unsigned WAIT_LIMIT = 1u << 22;        // bounded mbarrier polls, then an error flag
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}"
+               ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+// the same with an L2 evict-first policy: the tangent is read once per
+// iteration and should not push the CG vectors the next kernels read out of L2
+__device__ __forceinline__ void bulk_g2s_stream(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("{\n .reg .b64 pol;\n createpolicy.fractional.L2::evict_first.b64 pol, 1.0;\n"
+               " cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], pol;\n}"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+// wait for the phase of the given parity; false after WAIT_LIMIT polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  for (unsigned i = 0; i < WAIT_LIMIT; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// issue the 99 row copies of tile `tile` into a stage buffer (threads 0..98)
+__device__ __forceinline__ void ta_issue(const float* __restrict__ K, const float* __restrict__ r,
+                                         const float* __restrict__ p, size_t nvox, long tile, float* buf,
+                                         uint64_t* bar) {
+  const size_t v0 = (size_t)tile * TA_TV;
+  const size_t nv = (nvox - v0) < (size_t)TA_TV ? nvox - v0 : (size_t)TA_TV;
+  const unsigned bytes = (unsigned)(nv * sizeof(float));   // nvox is a multiple of 4: a 16-byte multiple
+  if (threadIdx.x == 0) mbar_expect_tx(bar, TA_ROWS * bytes);
+  const int e = threadIdx.x;
+  if (e < TA_ROWS) {
+    if (e < 81)
+      bulk_g2s_stream(buf + e * TA_TV, K + (size_t)e * nvox + v0, bytes, bar);
+    else
+      bulk_g2s(buf + e * TA_TV, (e < 90 ? r + (size_t)(e - 81) * nvox : p + (size_t)(e - 90) * nvox) + v0, bytes, bar);
+  }
+}
+
+__global__ void __launch_bounds__(TA_TV, 1) k_tangent_apply32_tma(size_t nvox, const float* __restrict__ K,
+                                                                 const float* __restrict__ r, float* __restrict__ p,
+                                                                 float* __restrict__ t, double* __restrict__ ds,
+                                                                 double* __restrict__ partial,
+                                                                 unsigned int* __restrict__ ticket) {
+  extern __shared__ __align__(128) unsigned char ta_smem[];
+  float* stage[2] = {reinterpret_cast<float*>(ta_smem), reinterpret_cast<float*>(ta_smem) + TA_STAGE};
+  uint64_t* bar = reinterpret_cast<uint64_t*>(ta_smem + 2 * (size_t)TA_STAGE_BYTES);
+  __shared__ double sh[320];
+  if (ds[DS_DONE] != 0.0) return;
+  const bool first = ds[DS_ITERS] == 0.0;
+  const float beta = first ? 0.0f : (float)ds[DS_BETA];
+  const long ntiles = (long)((nvox + TA_TV - 1) / TA_TV);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+  }
+  __syncthreads();
+  long tile = blockIdx.x;
+  if (tile < ntiles) ta_issue(K, r, p, nvox, tile, stage[0], &bar[0]);
+  if (tile + gridDim.x < ntiles) ta_issue(K, r, p, nvox, tile + gridDim.x, stage[1], &bar[1]);
+  float acc = 0.0f;
+  bool ok = true;
+  unsigned phase[2] = {0u, 0u};
+  for (int k = 0; tile < ntiles; tile += gridDim.x, ++k) {
+    const int b = k & 1;
+    // the decision to go on is the whole block's: a barrier inside the loop follows
+    if (!__syncthreads_and(mbar_wait(&bar[b], phase[b]) ? 1 : 0)) { ok = false; break; }
+    phase[b] ^= 1u;
+    const size_t v = (size_t)tile * TA_TV + threadIdx.x;
+    if (v < nvox) {
+      const float* Ks = stage[b];
+      float pv[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        const float rv = Ks[(81 + c) * TA_TV + threadIdx.x];
+        pv[c] = first ? rv : fmaf(beta, Ks[(90 + c) * TA_TV + threadIdx.x], rv);
+        p[c * nvox + v] = pv[c];
+      }
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        float sacc = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) sacc = fmaf(Ks[(9 * i + j) * TA_TV + threadIdx.x], pv[j], sacc);
+        t[i * nvox + v] = sacc;
+        acc = fmaf(pv[i], sacc, acc);
+      }
+    }
+    __syncthreads();                              // every thread is done with this stage
+    const long next = tile + 2 * (long)gridDim.x;
+    if (next < ntiles) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      ta_issue(K, r, p, nvox, next, stage[b], &bar[b]);
+    }
+  }
+  if (!ok) {
+    // a copy never completed: flag it, give both stages a bounded wait and leave
+    if (threadIdx.x == 0) ds[DS_ERR] = 1.0;
+    mbar_wait(&bar[0], phase[0]);
+    mbar_wait(&bar[1], phase[1]);
+  }
+  const double s = blk_sum_v<float>(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  const double tot = last_block_sum(partial, ticket, sh);
+  if (threadIdx.x == 0 && !isnan(tot)) {
+    ds[DS_PKP] = tot;
+    ds[DS_ALPHA] = ds[DS_RR] / tot;
+  }
+}
+
 // x32 = 0; r32 = -R (rounded); rr; stop = eta^2 rr; iteration count 0
 __global__ void __launch_bounds__(RVE_RED_THREADS) k_cg_init32(size_t n, float* __restrict__ x, float* __restrict__ r,
                                                                const double* __restrict__ R, double* __restrict__ ds,
@@ -492,12 +626,21 @@ cudaError_t launch_output_field(const rve_s* h, int which, const double* P, cons
   return cudaGetLastError();
 }
 
+cudaError_t vec_init() {
+  return cudaFuncSetAttribute(k_tangent_apply32_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TA_SMEM);
+}
+
 cudaError_t launch_tangent_apply32(const rve_s* h, cudaStream_t s) {
   {
     ProfScope ps_(h, RVE_K_TANGENT_APPLY, s);
-    k_tangent_apply32<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, reinterpret_cast<const float*>(h->K[h->cur]),
-                                                                 h->r32, h->p32, h->t32, h->dscal, h->partial,
-                                                                 (unsigned int*)(h->dcount + 4));
+    if (h->tma_apply)   // persistent: one block per SM
+      k_tangent_apply32_tma<<<h->num_sms, TA_TV, TA_SMEM, s>>>(h->nvox, reinterpret_cast<const float*>(h->K[h->cur]),
+                                                               h->r32, h->p32, h->t32, h->dscal, h->partial,
+                                                               (unsigned int*)(h->dcount + 4));
+    else
+      k_tangent_apply32<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, reinterpret_cast<const float*>(h->K[h->cur]),
+                                                                   h->r32, h->p32, h->t32, h->dscal, h->partial,
+                                                                   (unsigned int*)(h->dcount + 4));
   }
   return cudaGetLastError();
 }
