@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                     help="replay chunks of CG iterations as captured CUDA graphs")
+    ap.add_argument("--autotune", type=int, default=None, choices=[0, 1],
+                    help="time candidate launch shapes at create (default: on for the sweep, off otherwise)")
     ap.add_argument("--sensitivity", action="store_true",
                     help="time the increments with and without d<P>/d(tau0, K, alpha, b) and report the ratio")
     ap.add_argument("--no-e2e", action="store_true")
@@ -330,7 +332,8 @@ def run_sweep(a):
     rves = []
     for w in wls:
         gid, quat, mat = w.inputs()
-        rves.append(pkg.RVE(gid, quat, mat, w.edge, own_stream=True, precision=prec, graphs=a.graphs))
+        rves.append(pkg.RVE(gid, quat, mat, w.edge, own_stream=True, precision=prec, graphs=a.graphs,
+                            autotune=1 if a.autotune is None else a.autotune))
     mask = rvegen.UNIAXIAL_X_MASK
     dF = [w.dFbar() for w in wls]
     dts = [w.dt for w in wls]
@@ -372,7 +375,8 @@ def run_sweep(a):
                                    "2 % tension in 20 increments, L = 100 um, batched (one stream per RVE)",
                        "voxels": int(sum(w.n ** 3 for w in wls))},
             "gpu_launches": launches, "clocks": clocks.summary(),
-            "detail": {"cg_iters_per_increment_all_rves": cg / a.steps, "flow_stress": curve}}
+            "detail": {"cg_iters_per_increment_all_rves": cg / a.steps, "flow_stress": curve,
+                       "launch_shapes": [r.tuning() for r in rves]}}
     for r in rves:
         r.close()
     print(json.dumps(line))
@@ -447,7 +451,8 @@ def main():
     prec = 1 if a.precision == "mixed" else 0
     # a stream of the library's own: the CG chunks are replayed as CUDA graphs,
     # which the legacy default stream cannot capture
-    rve = pkg.RVE(gid, quat, mat, wl.edge, device=dev, precision=prec, own_stream=True, graphs=a.graphs)
+    rve = pkg.RVE(gid, quat, mat, wl.edge, device=dev, precision=prec, own_stream=True, graphs=a.graphs,
+                  autotune=a.autotune or 0)
     stream = rve.stream
     for _ in range(a.warmup):
         rve.step(wl.dFbar(), mask, Pbar, wl.dt)
@@ -479,6 +484,7 @@ def main():
     value = nvox * cg_all / (ms_max / 1e3)
     P_macro, sig_macro = rve.macro_stress()
     launches = int(sum(v[0] for v in stats.values()))
+    shapes = rve.tuning()
     rve.close()
     del rve
     torch.cuda.empty_cache()
@@ -489,7 +495,8 @@ def main():
         sig_h = torch.empty((9, nvox), dtype=torch.float64).pin_memory()
         gnd_h = torch.empty((12, nvox), dtype=torch.float64).pin_memory()
         load_h = torch.empty(9 + 9, dtype=torch.float64).pin_memory().numpy()
-        r2 = pkg.RVE(gid, quat, mat, wl.edge, device=dev, precision=prec, own_stream=True, graphs=a.graphs)
+        r2 = pkg.RVE(gid, quat, mat, wl.edge, device=dev, precision=prec, own_stream=True, graphs=a.graphs,
+                     autotune=a.autotune or 0)
         cg2 = 0
         h2d = 9 * 8 + 9 + 9 * 8
         d2h = sig_h.numel() * 8 + gnd_h.numel() * 8 + 2 * 9 * 8
@@ -549,7 +556,7 @@ def main():
             "data": "synthetic", "config": config,
             "e2e": e2e, "gpu_launches": launches, "roofline": roof_line, "cpu_baseline": cpu,
             "clocks": clocks.summary(),
-            "detail": {"cuda_graphs": bool(a.graphs),
+            "detail": {"cuda_graphs": bool(a.graphs), "launch_shapes": shapes,
                        "voxel_increments_per_s": world * nvox * a.steps / (ms_max / 1e3),
                        "cg_iters_per_increment": cg_total / a.steps,
                        "newton_iters_per_increment": newton_total / a.steps,

@@ -96,6 +96,11 @@ typedef struct {
                             default stream; ignored there).  Results are bit-identical. */
   int32_t tma;           /* nonzero: the FP32 tangent apply streams the tangent through shared
                             memory with bulk asynchronous copies (precision 1 only) */
+  int32_t autotune;      /* nonzero: rve_create times candidate launch shapes on the handle's own
+                            buffers and keeps the fastest (grid of the divergence stencil, FFT
+                            tile sizes, staged or plain FP32 tangent apply; see rve_get_tuning).
+                            The choice follows measured times, so two tuned handles may differ in
+                            reduction order: equal results to round-off, not bit for bit. */
 } rve_options;
 
 #define RVE_MAX_NEWTON_LOG 64
@@ -232,6 +237,11 @@ enum {
   RVE_K_REDUCE = 8, RVE_K_OTHER = 9, RVE_K_STENCIL = 10, RVE_K_TANGENT_BUILD = 11, RVE_K_COUNT = 12
 };
 rve_status rve_profile(rve_t* rve, int enable);
+/* The launch shapes in use: out[0] grid cap of the divergence stencil (blocks),
+ * out[1] block count the FFT tile rules aim for, out[2] 1 if the FP32 tangent
+ * apply is staged by bulk copies, out[3] 1 if the autotuner chose them
+ * (host array of 4). */
+rve_status rve_get_tuning(rve_t* rve, int32_t out[4]);
 rve_status rve_kernel_stats(rve_t* rve, int64_t* launches, double* ms);
 
 /* Allocation-free Galerkin projection (no counterpart in the paper; an

@@ -45,7 +45,7 @@ class rve_options(C.Structure):
                 ("local_tol", C.c_double), ("max_newton", C.c_int32), ("max_cg", C.c_int32),
                 ("max_local", C.c_int32), ("max_halvings", C.c_int32), ("extrapolate", C.c_int32),
                 ("precision", C.c_int32), ("cg_adaptive", C.c_int32), ("krylov", C.c_int32),
-                ("graphs", C.c_int32), ("tma", C.c_int32)]
+                ("graphs", C.c_int32), ("tma", C.c_int32), ("autotune", C.c_int32)]
 
 
 class rve_step_info(C.Structure):
@@ -75,6 +75,7 @@ _SIGS = {
     "rve_checkpoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "rve_restore": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "rve_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "rve_get_tuning": (C.c_int, [C.c_void_p, C.c_void_p]),
     "rve_kernel_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "rve_project_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p]),
@@ -244,7 +245,7 @@ def rve_destroy(h):
 
 # ---- handle wrapper ---------------------------------------------------------
 DEFAULT_OPTIONS = dict(newton_tol=1e-11, cg_tol=1e-11, local_tol=1e-14, max_newton=100, max_cg=2000,
-                       max_local=60, max_halvings=12, extrapolate=1, precision=0, cg_adaptive=1, krylov=0, graphs=1, tma=1)
+                       max_local=60, max_halvings=12, extrapolate=1, precision=0, cg_adaptive=1, krylov=0, graphs=1, tma=1, autotune=0)
 
 
 def make_material(m) -> rve_material:
@@ -344,6 +345,12 @@ class RVE:
         base = self.sens_workspace.data_ptr()
         aligned = (base + 255) // 256 * 256
         self._check(rve_sensitivity_enable(self.h, aligned, n, tol), "rve_sensitivity_enable")
+
+    def tuning(self):
+        """Launch shapes in use: divergence grid cap, FFT fill target, staged FP32 apply, autotuned."""
+        out = np.zeros(4, dtype=np.int32)
+        self._check(load_library().rve_get_tuning(self.h, _ptr(out)), "rve_get_tuning")
+        return dict(div_blocks=int(out[0]), fft_fill=int(out[1]), tma=bool(out[2]), autotuned=bool(out[3]))
 
     def stress_sensitivity(self):
         """d<P>/d theta of the last increment, shape (4, 3, 3), theta = PARAMS."""

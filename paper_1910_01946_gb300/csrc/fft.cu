@@ -360,32 +360,31 @@ __global__ void __launch_bounds__(256) k_fft_z_op(V2<R>* __restrict__ spec, int 
 // Tile sizes: as large as shared memory allows (up to 1024 complex per
 // transform batch, 512 in the z pass that holds three fields), shrunk while
 // the grid would fill less than four blocks per SM, down to 256 elements.
-constexpr int FILL_BLOCKS = 4 * 152;
 
-int rows_per_block(int n0, int n1, int n2, int nf) {
+int rows_per_block(int n0, int n1, int n2, int nf, int fill) {
   int r = 1024 / n0;
   if (r < 1) r = 1;
   if (r > n1 / 2) r = n1 / 2;
   while (r > 1 && (n1 / 2) % r) --r;
-  while (r > 1 && (long)(n1 / 2 / r) * n2 * nf < FILL_BLOCKS && r * n0 > 256) {
+  while (r > 1 && (long)(n1 / 2 / r) * n2 * nf < fill && r * n0 > 256) {
     int q = r / 2;
     while (q > 1 && (n1 / 2) % q) --q;
     r = q;
   }
   return r;
 }
-int tile_y(int n1, int n2, int nkx, int nf) {
+int tile_y(int n1, int n2, int nkx, int nf, int fill) {
   int t = 1024 / n1;
   if (t > 16) t = 16;
   if (t < 1) t = 1;
-  while (t > 1 && (long)((nkx + t - 1) / t) * n2 * nf < FILL_BLOCKS && t * n1 > 256) t /= 2;
+  while (t > 1 && (long)((nkx + t - 1) / t) * n2 * nf < fill && t * n1 > 256) t /= 2;
   return t;
 }
-int tile_z(int n1, int n2, int nkx, int nf) {
+int tile_z(int n1, int n2, int nkx, int nf, int fill) {
   int t = 512 / n2;
   if (t > 16) t = 16;
   if (t < 1) t = 1;
-  while (t > 1 && (long)((nkx + t - 1) / t) * n1 * (nf / 3) < FILL_BLOCKS && 3 * t * n2 > 256) t /= 2;
+  while (t > 1 && (long)((nkx + t - 1) / t) * n1 * (nf / 3) < fill && 3 * t * n2 > 256) t /= 2;
   return t;
 }
 // threads for a block holding `elems` complex values (radix-4 butterflies: elems / 4)
@@ -413,7 +412,7 @@ template <> float2* spect<float>(const rve_s* h) { return h->spec32; }
 
 template <typename R>
 cudaError_t fwd(const rve_s* h, const R* in, cudaStream_t s, const double* done, int nf) {
-  const int rpb = rows_per_block(h->n0, h->n1, h->n2, nf);
+  const int rpb = rows_per_block(h->n0, h->n1, h->n2, nf, h->fft_fill);
   dim3 gx(h->n1 / 2 / rpb, h->n2, nf);
   size_t shx = 2 * (size_t)rpb * h->n0 * sizeof(CX<R>);
   {
@@ -421,7 +420,7 @@ cudaError_t fwd(const rve_s* h, const R* in, cudaStream_t s, const double* done,
     k_fft_x_r2c<R><<<gx, threads_for(rpb * h->n0), shx, s>>>(in, spect<R>(h), h->n0, h->n1, h->n2, h->nkx, rpb,
                                                              to_dev(h->plan[0]), twt<R>(h, 0), done);
   }
-  const int ty = tile_y(h->n1, h->n2, h->nkx, nf);
+  const int ty = tile_y(h->n1, h->n2, h->nkx, nf, h->fft_fill);
   dim3 gy((h->nkx + ty - 1) / ty, h->n2, nf);
   size_t shy = 2 * (size_t)ty * h->n1 * sizeof(CX<R>);
   {
@@ -434,7 +433,7 @@ cudaError_t fwd(const rve_s* h, const R* in, cudaStream_t s, const double* done,
 
 template <typename R>
 cudaError_t zop(const rve_s* h, const SpecParams& sp, cudaStream_t s, const double* done, int nf) {
-  const int tz = tile_z(h->n1, h->n2, h->nkx, nf);
+  const int tz = tile_z(h->n1, h->n2, h->nkx, nf, h->fft_fill);
   dim3 g((h->nkx + tz - 1) / tz, h->n1, nf / 3);
   size_t sh = 2 * 3 * (size_t)tz * h->n2 * sizeof(CX<R>);
   const int zthreads = threads_for(3 * tz * h->n2);
@@ -448,7 +447,7 @@ cudaError_t zop(const rve_s* h, const SpecParams& sp, cudaStream_t s, const doub
 
 template <typename R>
 cudaError_t inv(const rve_s* h, R* out, cudaStream_t s, const double* done, int nf) {
-  const int ty = tile_y(h->n1, h->n2, h->nkx, nf);
+  const int ty = tile_y(h->n1, h->n2, h->nkx, nf, h->fft_fill);
   dim3 gy((h->nkx + ty - 1) / ty, h->n2, nf);
   size_t shy = 2 * (size_t)ty * h->n1 * sizeof(CX<R>);
   {
@@ -456,7 +455,7 @@ cudaError_t inv(const rve_s* h, R* out, cudaStream_t s, const double* done, int 
     k_fft_y<+1, R><<<gy, threads_for(ty * h->n1), shy, s>>>(spect<R>(h), h->n1, h->n2, h->nkx, ty,
                                                             to_dev(h->plan[1]), twt<R>(h, 1), done);
   }
-  const int rpb = rows_per_block(h->n0, h->n1, h->n2, nf);
+  const int rpb = rows_per_block(h->n0, h->n1, h->n2, nf, h->fft_fill);
   dim3 gx(h->n1 / 2 / rpb, h->n2, nf);
   size_t shx = 2 * (size_t)rpb * h->n0 * sizeof(CX<R>);
   {

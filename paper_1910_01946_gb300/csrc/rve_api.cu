@@ -553,6 +553,93 @@ rve_status sens_update(rve_s* h, const uint8_t* mask, double dt) {
   return RVE_OK;
 }
 
+// Launch-shape autotuner (rve_options.autotune): at create, on the handle's
+// own buffers, time each candidate of three choices on its stream and keep
+// the fastest -- the grid cap of the divergence stencil, the block count the
+// FFT tile rules aim for, and (mixed precision) the staged or the plain
+// tangent apply.  Device scalars are reset afterwards; the handle's state is
+// as after an untuned create.
+rve_status autotune(rve_s* h) {
+  cudaStream_t st = h->stream;
+  cudaEvent_t e0, e1;
+  RVE_CUDA(h, cudaEventCreate(&e0));
+  RVE_CUDA(h, cudaEventCreate(&e1));
+  const bool f32 = h->opt.precision == 1;
+  const uint8_t mask[9] = {1, 0, 0, 1, 0, 0, 1, 1, 0};
+  if (f32) {
+    RVE_CUDA(h, cudaMemsetAsync(h->t32, 0, 9 * h->nvox * sizeof(float), st));
+    RVE_CUDA(h, cudaMemsetAsync(h->r32, 0, 9 * h->nvox * sizeof(float), st));
+  }
+  auto timed = [&](auto&& launch, float* ms) -> rve_status {
+    for (int w = 0; w < 2; ++w) RVE_CUDA(h, launch());
+    RVE_CUDA(h, cudaEventRecord(e0, st));
+    for (int k = 0; k < 5; ++k) RVE_CUDA(h, launch());
+    RVE_CUDA(h, cudaEventRecord(e1, st));
+    RVE_CUDA(h, cudaEventSynchronize(e1));
+    RVE_CUDA(h, cudaEventElapsedTime(ms, e0, e1));
+    return RVE_OK;
+  };
+  const int sms = h->num_sms;
+  // divergence grid cap
+  {
+    const int cand[5] = {2 * sms, 3 * sms, 4 * sms, 6 * sms, 8 * sms};
+    float best = 1e30f;
+    int pick = h->div_blocks;
+    for (int c : cand) {
+      if (c > 4096) continue;
+      h->div_blocks = c;
+      float ms = 0.f;
+      RVE_TRY(timed([&]() {
+        return f32 ? launch_div32(h, h->t32, h->du32, kept_means(mask), st)
+                   : launch_div(h, h->F, h->q, 0, kept_means(mask), st);
+      }, &ms));
+      if (ms < best) { best = ms; pick = c; }
+    }
+    h->div_blocks = pick;
+  }
+  // FFT tile fill target (forward, Laplace solve, inverse of three fields)
+  {
+    SpecParams sp = project_params(h, mask, nullptr, nullptr);
+    sp.op = OP_LAPINV;
+    const int cand[4] = {2 * sms, 4 * sms, 8 * sms, 16 * sms};
+    float best = 1e30f;
+    int pick = h->fft_fill;
+    for (int c : cand) {
+      h->fft_fill = c;
+      float ms = 0.f;
+      RVE_TRY(timed([&]() -> cudaError_t {
+        if (f32) {
+          if (cudaError_t e = launch_fft_forward32(h, h->du32, st, nullptr)) return e;
+          if (cudaError_t e = launch_fft_lapinv32(h, sp, st, nullptr)) return e;
+          return launch_fft_inverse32(h, h->du32 + 3 * h->nvox, st, nullptr);
+        }
+        if (cudaError_t e = launch_fft_forward(h, h->q, st, nullptr, 3)) return e;
+        if (cudaError_t e = launch_fft_op(h, sp, st, nullptr, 3)) return e;
+        return launch_fft_inverse(h, h->q + 3 * h->nvox, st, nullptr, 3);
+      }, &ms));
+      if (ms < best) { best = ms; pick = c; }
+    }
+    h->fft_fill = pick;
+  }
+  // staged or plain FP32 tangent apply (the tangent buffer's contents do not matter)
+  if (f32 && h->tma_apply) {
+    float ms[2] = {0.f, 0.f};
+    for (int v = 0; v < 2; ++v) {
+      h->tma_apply = v == 1;
+      RVE_TRY(timed([&]() { return launch_tangent_apply32(h, st); }, &ms[v]));
+    }
+    h->tma_apply = ms[1] <= ms[0];
+  }
+  RVE_CUDA(h, cudaMemsetAsync(h->dscal, 0, 64 * sizeof(double), st));
+  RVE_CUDA(h, cudaMemsetAsync(h->dcount, 0, 16 * sizeof(int32_t), st));
+  RVE_CUDA(h, cudaStreamSynchronize(st));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->prof.reset();
+  h->autotuned = true;
+  return RVE_OK;
+}
+
 // The tangent of the evaluation that ended the last increment, built on
 // request (rve_step skips it): same F, S, frozen hardening and step.
 rve_status build_stale_tangent(rve_s* h) {
@@ -809,6 +896,7 @@ rve_status rve_create(const int32_t* grain_id, int n0, int n1, int n2, const dou
             bad(cudaMemsetAsync(h->dcount, 0, 16 * sizeof(int32_t), s)) ||
             bad(cudaStreamSynchronize(s));
   }
+  if (!fail_ && opt->autotune) fail_ = autotune(h) != RVE_OK;
   if (fail_) {
     cudaFreeHost(h->hscal);
     cudaFreeHost(h->hcount);
@@ -1218,6 +1306,15 @@ rve_status rve_get_stress_sensitivity(rve_t* h, double dP[RVE_NTHETA * 9]) {
   if (!h || !dP) return RVE_EINVAL;
   if (!h->sens_on || !h->sens_valid) return fail(h, RVE_EINVAL, "no sensitivity of a converged increment");
   for (int k = 0; k < RVE_NTHETA * 9; ++k) dP[k] = h->sens_dP[k];
+  return RVE_OK;
+}
+
+rve_status rve_get_tuning(rve_t* h, int32_t out[4]) {
+  if (!h || !out) return RVE_EINVAL;
+  out[0] = h->div_blocks;
+  out[1] = h->fft_fill;
+  out[2] = h->tma_apply ? 1 : 0;
+  out[3] = h->autotuned ? 1 : 0;
   return RVE_OK;
 }
 

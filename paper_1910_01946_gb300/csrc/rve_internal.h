@@ -124,6 +124,10 @@ struct rve_s {
   CgGraph graphs[RVE_CG_GRAPHS];
   int graph_next = 0;
   int num_sms = 152;        // of the handle's device
+  // launch shapes (rve_options.autotune times candidates at create):
+  int div_blocks = 4 * 152; // grid cap of the divergence stencil
+  int fft_fill = 4 * 152;   // block count the FFT tile rules aim for
+  bool autotuned = false;
   bool tma_apply = false;   // FP32 tangent apply staged by bulk copies (rve_options.tma)
   // forward-mode sensitivities (rve_sensitivity_enable): state tangents
   // dFp (9) and d rho_SSD (12) per parameter, double-buffered so that a

@@ -32,10 +32,10 @@ struct Grid3 {
 constexpr int NT = 128;
 constexpr int SMAX = 196;       // max (ty + 1)(tx + 1) over tx in {2, 4, ..., 32}
 constexpr int MAX_BLOCKS = 4096;
-// k_div reduces nine means per thread at the end (a warp-shuffle tree of five
-// FP64 additions each): its grid is capped at four blocks per SM so that each
-// thread first accumulates several tiles and the reduction is amortised
-constexpr int DIV_BLOCKS = 4 * 152;
+// k_div reduces the field means per thread at the end: its grid is capped
+// (rve_s::div_blocks, four blocks per SM unless the autotuner picks another)
+// so that each thread first accumulates several tiles and the reduction is
+// amortised
 
 struct Tiling {
   int tx, ty, bx, by, ntiles, nblocks;
@@ -280,7 +280,7 @@ cudaError_t launch_div(const rve_s* h, const double* X, double* d, int check_don
                        cudaStream_t s) {
   Tiling T = tiling_of(h);
   if ((T.tx + 1) * (T.ty + 1) > SMAX) return cudaErrorInvalidValue;   // n0 odd: not a valid grid
-  if (T.nblocks > DIV_BLOCKS) T.nblocks = DIV_BLOCKS;
+  if (T.nblocks > h->div_blocks) T.nblocks = h->div_blocks;
   {
     ProfScope ps_(h, RVE_K_STENCIL, s);
     k_div<double><<<T.nblocks, dim3(T.tx, T.ty), 0, s>>>(grid_of(h), T, X, d, h->dscal, h->partial,
@@ -319,7 +319,7 @@ cudaError_t launch_div32(const rve_s* h, const float* X, float* d, unsigned mean
   // measured slower (41.5 against 34.6 us) than a few tiles per block
   Tiling T = tiling_of(h);
   if ((T.tx + 1) * (T.ty + 1) > SMAX) return cudaErrorInvalidValue;   // n0 odd: not a valid grid
-  if (T.nblocks > DIV_BLOCKS) T.nblocks = DIV_BLOCKS;
+  if (T.nblocks > h->div_blocks) T.nblocks = h->div_blocks;
   {
     ProfScope ps_(h, RVE_K_STENCIL, s);
     k_div<float><<<T.nblocks, dim3(T.tx, T.ty), 0, s>>>(grid_of(h), T, X, d, h->dscal, h->partial,

@@ -47,6 +47,6 @@ def test_workspace_bytes_validation(lib):
 def test_struct_layouts_match_header():
     import ctypes as C
     import paper_1910_01946_gb300 as pkg
-    assert C.sizeof(pkg.rve_options) == 4 * 8 + 10 * 4   # ten int32 fields
+    assert C.sizeof(pkg.rve_options) == 4 * 8 + 11 * 4 + 4   # eleven int32 fields and tail padding
     assert C.sizeof(pkg.rve_material) == 7 * 8 + 6 * 8 + 8 + 5 * 8 + 8
     assert pkg.rve_step_info.local_iters_total.offset == 32 and pkg.rve_step_info.residual.offset == 48

@@ -7,6 +7,7 @@
 * A failing handle in a batch reports its own status and leaves the others
   and itself usable (atomic steps).
 * CG chunks replayed as CUDA graphs are bit-identical to host launches.
+* Handles whose launch shapes the autotuner picked give the same increments.
 * Size effect (Sec. 3): with the GND density switched off the response does
   not depend on the RVE's physical size at all; with it on, the smaller
   grains harden more."""
@@ -84,6 +85,27 @@ def test_cg_graph_replay_is_bit_identical(pkg, precision):
     a.step(wl.dFbar(), MASK, np.zeros(9), wl.dt)
     b.step(wl.dFbar(), MASK, np.zeros(9), wl.dt)
     assert np.array_equal(a.field("F"), b.field("F"))
+    a.close(); b.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_autotuned_handle_matches_default(pkg, precision):
+    """rve_options.autotune picks launch shapes from measured times at create;
+    the tuned handle converges to the same increments as the default shapes
+    (to round-off: the reduction order may differ)."""
+    wl = WLS[3]
+    a = make(pkg, wl, autotune=1, precision=precision)
+    b = make(pkg, wl, precision=precision)
+    t = a.tuning()
+    assert t["autotuned"] and not b.tuning()["autotuned"]
+    sms = 152 if t["div_blocks"] % 152 == 0 else None
+    assert t["div_blocks"] > 0 and t["fft_fill"] > 0 and sms is not None
+    for k in range(wl.increments):
+        assert a.step(wl.dFbar(), MASK, np.zeros(9), wl.dt)["converged"]
+        assert b.step(wl.dFbar(), MASK, np.zeros(9), wl.dt)["converged"]
+    for name in ("F", "P", "FP", "RHO_SSD"):
+        ra, rb = a.field(name), b.field(name)
+        assert np.abs(ra - rb).max() <= 1e-9 * np.abs(rb).max(), name
     a.close(); b.close()
 
 
