@@ -582,11 +582,13 @@ rve_status autotune(rve_s* h) {
   const int sms = h->num_sms;
   // divergence grid cap
   {
-    const int cand[5] = {2 * sms, 3 * sms, 4 * sms, 6 * sms, 8 * sms};
+    // multiples of the SM count, and grids that split the tiles evenly
+    const int nt = stencil_tiles(h);
+    const int cand[9] = {2 * sms, 3 * sms, 4 * sms, 6 * sms, 8 * sms, nt / 8, nt / 4, nt / 2, nt};
     float best = 1e30f;
     int pick = h->div_blocks;
     for (int c : cand) {
-      if (c > 4096) continue;
+      if (c < 1 || c > 4096) continue;
       h->div_blocks = c;
       float ms = 0.f;
       RVE_TRY(timed([&]() {

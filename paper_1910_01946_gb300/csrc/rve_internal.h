@@ -191,6 +191,8 @@ cudaError_t launch_fft_lapinv32(const rve_s* h, const SpecParams& sp, cudaStream
 cudaError_t launch_fft_inverse32(const rve_s* h, float* out, cudaStream_t s, const double* done);
 
 // ---- stencil.cu: G* = D (D^H D)^-1 D^H with real-space rotated-scheme stencils ----
+// number of tiles the stencils cover (their grids loop over them)
+int stencil_tiles(const rve_s* h);
 // mean_mask: bit c set = the mean of field c is reduced into ds[DS_XMEAN + c]
 // (others read 0)
 cudaError_t launch_div(const rve_s* h, const double* X, double* d, int check_done, unsigned mean_mask,

@@ -276,6 +276,8 @@ ZeroMode zero_mode(const uint8_t* mask, const double* shift) {
 
 }  // namespace
 
+int stencil_tiles(const rve_s* h) { return tiling_of(h).ntiles; }
+
 cudaError_t launch_div(const rve_s* h, const double* X, double* d, int check_done, unsigned mean_mask,
                        cudaStream_t s) {
   Tiling T = tiling_of(h);
