@@ -176,7 +176,8 @@ rve_status rve_create(const int32_t* grain_id, int n0, int n1, int n2,
 rve_status rve_step(rve_t* rve, const double dFbar[9], const uint8_t strain_mask[9],
                     const double Pbar[9], double dt, rve_step_info* info);
 
-/* Batched increments: n independent handles (different sizes, grain counts,
+/* Batched increments (the grain-size study of Sec. 3-4 runs many RVEs of
+ * different sizes): n independent handles (different sizes, grain counts,
  * materials) each advance one increment, concurrently.  One host thread per
  * handle drives that handle's own stream, so the kernels of different RVEs
  * overlap on the GPU (the batched grain-size sweep).  dFbar, strain_mask and
@@ -224,7 +225,8 @@ size_t rve_checkpoint_bytes(const rve_t* rve);
 rve_status rve_checkpoint(rve_t* rve, void* host_buf, size_t bytes);
 rve_status rve_restore(rve_t* rve, const void* host_buf, size_t bytes);
 
-/* Kernel accounting.  Every kernel launch is counted per category (always on).
+/* Kernel accounting (no counterpart in the paper: instrumentation for the
+ * measurements).  Every kernel launch is counted per category (always on).
  * With rve_profile(rve, 1) each launch is also bracketed by CUDA events on
  * the handle's stream and its device time accumulated per category (the
  * events are resolved at the library's own host synchronisation points);
@@ -237,7 +239,8 @@ enum {
   RVE_K_REDUCE = 8, RVE_K_OTHER = 9, RVE_K_STENCIL = 10, RVE_K_TANGENT_BUILD = 11, RVE_K_COUNT = 12
 };
 rve_status rve_profile(rve_t* rve, int enable);
-/* The launch shapes in use: out[0] grid cap of the divergence stencil (blocks),
+/* The launch shapes in use (no counterpart in the paper): out[0] grid cap of
+ * the divergence stencil (blocks),
  * out[1] block count the FFT tile rules aim for, out[2] 1 if the FP32 tangent
  * apply is staged by bulk copies, out[3] 1 if the autotuner chose them
  * (host array of 4). */
