@@ -194,7 +194,7 @@ def roofline(stats, shape, peaks, local=None, prec=0):
 # workload; keyed by (category, precision).  Kernels changed since that
 # capture have no entry (reported as null), as do other grid sizes.
 TRAFFIC_64 = {
-    ("tangent_apply", 0): 207.66e6 + 5.11e6,   # K : p reads its algorithmic 207.6 MB
+    ("tangent_apply", 0): 207.66e6 + 5.10e6,   # K : p reads its algorithmic 207.6 MB
     ("tangent_apply", 1): 103.84e6 + 3.53e6,   # TMA-staged FP32 apply (float K, r, p)
     ("constitutive", 0): 98.92e6 + 50.16e6,    # k_local (the same kernel in both precisions)
     ("constitutive", 1): 98.92e6 + 50.16e6,

@@ -46,7 +46,7 @@ __device__ __forceinline__ double last_block_sum(const double* partial, unsigned
 
 // p = r (first) or r + beta p; t = K : p; pKp = p . t; alpha = rr / pKp.
 // Returns at once when the CG loop has converged (done != 0).
-__global__ void __launch_bounds__(RVE_RED_THREADS, 2) k_tangent_apply(size_t nvox, const double* __restrict__ K,
+__global__ void __launch_bounds__(RVE_RED_THREADS, 3) k_tangent_apply(size_t nvox, const double* __restrict__ K,
                                                                       const double* __restrict__ r, double* __restrict__ p,
                                                                       double* __restrict__ t, double* __restrict__ ds,
                                                                       double* __restrict__ partial,
