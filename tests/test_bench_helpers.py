@@ -1,0 +1,42 @@
+"""Host logic of bench.py's roofline line (CPU only): which bound a kernel is
+rated against, and that the per-launch algorithmic figures follow from the
+per-voxel counts."""
+import importlib.util
+import os
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    return m
+
+
+def test_fp64_cg_kernels_are_alu_bound_and_fp32_ones_hbm_bound():
+    b = bench()
+    peaks = {"hbm_gbs": 6789.6}
+    shape = (64, 64, 64)
+    _, r64 = b.roofline({"tangent_apply": (100, 6.7)}, shape, peaks, prec=0)
+    assert r64["bound"] == "alu" and r64["unit"].startswith("GFLOP/s")
+    # 81 FMA for K : p, 9 for the p update, 9 for p . t per voxel
+    assert r64["algorithmic_flops"] == 64 ** 3 * 198
+    _, r32 = b.roofline({"tangent_apply": (100, 2.7)}, shape, peaks, prec=1)
+    assert r32["bound"] == "hbm" and r32["unit"] == "GB/s"
+    assert r32["algorithmic_bytes"] == r64["algorithmic_bytes"] / 2
+    assert abs(r32["achieved"] - r32["algorithmic_bytes"] / 27e-6 / 1e9) < 1e-6 * r32["achieved"]
+
+
+def test_dominant_kernel_and_share():
+    b = bench()
+    stats = {"tangent_apply": (10, 0.8), "stencil": (10, 0.5), "constitutive": (0, 0.0)}
+    dom, r = b.roofline(stats, (32, 32, 32), {"hbm_gbs": 6789.6})
+    assert dom == "tangent_apply" and abs(r["share"] - 0.8 / 1.3) < 1e-12 and r["launches"] == 10
+
+
+def test_traffic_table_names_known_categories():
+    b = bench()
+    cats = set(b.kernel_models(64, 64, 64, local=(1, 1, 1)))
+    for (cat, prec), v in b.TRAFFIC_64.items():
+        assert cat in cats and prec in (0, 1) and v > 0
