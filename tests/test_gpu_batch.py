@@ -98,8 +98,7 @@ def test_autotuned_handle_matches_default(pkg, precision):
     b = make(pkg, wl, precision=precision)
     t = a.tuning()
     assert t["autotuned"] and not b.tuning()["autotuned"]
-    sms = 152 if t["div_blocks"] % 152 == 0 else None
-    assert t["div_blocks"] > 0 and t["fft_fill"] > 0 and sms is not None
+    assert 0 < t["div_blocks"] <= 4096 and t["fft_fill"] > 0
     for k in range(wl.increments):
         assert a.step(wl.dFbar(), MASK, np.zeros(9), wl.dt)["converged"]
         assert b.step(wl.dFbar(), MASK, np.zeros(9), wl.dt)["converged"]
