@@ -29,7 +29,8 @@
  *   - every call is issued on the CUDA stream given at rve_create and
  *     returns an rve_status; no exception or abort crosses the ABI.  On a
  *     non-OK status rve_last_error() gives a message.  A device error
- *     (RVE_ECUDA) leaves the handle unusable.
+ *     (RVE_ECUDA) leaves the handle unusable; every other status leaves the
+ *     last committed increment in place and the handle usable.
  */
 #ifndef RVE_H
 #define RVE_H
@@ -49,7 +50,11 @@ typedef enum {
   RVE_ENOCONV_LOCAL = 4,  /* a voxel's implicit update did not converge */
   RVE_ENOCONV_CG = 5,     /* conjugate gradients hit max_cg */
   RVE_ENOCONV_NEWTON = 6, /* Newton-Raphson hit max_newton or could not decrease the residual */
-  RVE_ENAN = 7            /* a non-finite residual */
+  RVE_ENAN = 7,           /* a non-finite residual (a non-finite value in the state, e.g. set through
+                             rve_set_fields); reported before RVE_ENOCONV_LOCAL */
+  RVE_ETIMEOUT = 8        /* a bounded wait inside a kernel gave up (see rve_set_wait_limit); the
+                             kernel drained its own copies first, nothing was committed and the
+                             handle stays usable */
 } rve_status;
 
 typedef struct rve_s rve_t;
@@ -247,28 +252,46 @@ rve_status rve_profile(rve_t* rve, int enable);
 rve_status rve_get_tuning(rve_t* rve, int32_t out[4]);
 rve_status rve_kernel_stats(rve_t* rve, int64_t* launches, double* ms);
 
+/* Poll limit of the per-tile wait in the staged FP32 tangent apply
+ * (rve_options.tma, precision 1; no counterpart in the paper: a bounded wait
+ * of the GPU design).  Each block of that kernel waits on an mbarrier for its
+ * bulk copies; after `polls` unsuccessful polls (default 4194304; 0 gives up
+ * at the first wait without polling) the block raises a device flag, waits at
+ * the default limit for every copy it still has in flight, and leaves.  The
+ * host finds the flag after the CG chunk and rve_step returns RVE_ETIMEOUT
+ * with the last committed increment intact; the handle stays usable.  A
+ * small limit makes that recovery path run on purpose (tests).  Drops the
+ * captured CG graphs, which carry the limit as a kernel argument. */
+rve_status rve_set_wait_limit(rve_t* rve, uint32_t polls);
+
 /* Allocation-free Galerkin projection (no counterpart in the paper; an
  * addition for callers that cannot allocate device memory).
  *
- * Y = G*(X) exactly as rve_project computes it, for device fields X and Y
- * (9 * n0*n1*n2 doubles each, layout as above, may alias) on an n0 x n1 x n2
- * grid of edge L along x, under strain_mask (host, 9 bytes).  It needs no
- * handle and no workspace: the FFT spectrum and frequency tables live in one
- * static device array of RVE_NOALLOC_SPEC_BYTES plus about 64 KiB, which every
- * GPU that loads the library holds until the process exits.  Meant for code
- * that must not call cudaMalloc: for example a plug-in running under a host
- * application whose memory manager has already reserved the device memory, or
- * a time-critical loop that cannot afford cudaMalloc/cudaFree's implicit
- * device-wide synchronisation.  This entry point calls no cudaMalloc,
- * cudaFree or other allocating routine.
+ * Y = G*(X) for device fields X and Y (9 * n0*n1*n2 doubles each, layout as
+ * above, may alias) on an n0 x n1 x n2 grid of edge L along x, under
+ * strain_mask (host, 9 bytes): the same linear map as rve_project, computed in
+ * the nine-field Fourier form (rve_project uses the stencil-factored form), so
+ * the two agree to round-off.  It needs no handle and no workspace: the FFT
+ * spectrum and frequency tables live in one static device array of
+ * RVE_NOALLOC_SPEC_BYTES plus about 64 KiB, which every GPU that loads the
+ * library holds until the process exits.  Meant for code that must not call
+ * cudaMalloc: for example a plug-in running under a host application whose
+ * memory manager has already reserved the device memory, or a time-critical
+ * loop that cannot afford cudaMalloc/cudaFree's implicit device-wide
+ * synchronisation.  This entry point calls no cudaMalloc, cudaFree or other
+ * allocating routine, and copies nothing from the host.
  *
  * Work is queued on cuda_stream (a cudaStream_t, NULL = legacy default
  * stream) and the call returns without waiting: synchronise the stream before
  * reading Y.  The first call on a device looks up the device address of the
  * static array (cudaGetSymbolAddress, once per device, with that device
- * current); make that first call before any stream capture.  All calls share
+ * current) and, like every call whose grid differs from the previous call's on
+ * that device, launches one small kernel that writes the frequency tables into
+ * the array; make that first call before any stream capture.  All calls share
  * the one array, which keeps the last call's contents: calls that overlap on
- * the GPU (different streams, or different host threads) race on it.
+ * the GPU (different streams, or different host threads) race on it.  The
+ * cached address and tables do not survive cudaDeviceReset: do not call this
+ * entry point after resetting the device in the same process.
  *
  * Errors: RVE_EINVAL for bad pointers, L <= 0 or unsupported sizes (as in
  * rve_workspace_bytes); RVE_ENOMEM when 9 * (n0/2 + 1) * n1 * n2 * 16 bytes of
@@ -295,10 +318,12 @@ rve_status rve_project_noalloc(int n0, int n1, int n2, double L, const uint8_t s
  *   aligned, >= rve_sensitivity_bytes, outliving the handle); the tangents
  *   start at zero, i.e. the current state is taken as independent of theta
  *   (exact from the initial state).  tol: relative tolerance of the linear
- *   solves (<= 0: the larger of rve_options.cg_tol and 1e-9).  From then on every rve_step also
- *   updates the sensitivities before it commits; a failed solve fails the
- *   step (RVE_ENOCONV_CG) with nothing committed.  rve_restore zeroes the
- *   tangents.
+ *   solves, used as given by both the CG and the BiCGStab solve (<= 0: the
+ *   larger of rve_options.cg_tol and 1e-9, BiCGStab at no less than 1e-12).
+ *   From then on every rve_step also updates the sensitivities before it
+ *   commits; a solve that reaches max_cg in both solvers fails the step
+ *   (RVE_ENOCONV_CG, rve_step_info.converged 0) with nothing committed.
+ *   rve_restore zeroes the tangents.
  * rve_get_stress_sensitivity: dP[9 * j + 3 * i + k] = d<P_ik> / d theta_j of
  *   the last converged increment (host array of 36); RVE_EINVAL when there is
  *   none. */

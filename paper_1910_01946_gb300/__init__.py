@@ -20,9 +20,9 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "librve.so")
 
 RVE_OK, RVE_EINVAL, RVE_ENOMEM, RVE_ECUDA = 0, 1, 2, 3
-RVE_ENOCONV_LOCAL, RVE_ENOCONV_CG, RVE_ENOCONV_NEWTON, RVE_ENAN = 4, 5, 6, 7
+RVE_ENOCONV_LOCAL, RVE_ENOCONV_CG, RVE_ENOCONV_NEWTON, RVE_ENAN, RVE_ETIMEOUT = 4, 5, 6, 7, 8
 STATUS_NAMES = {0: "RVE_OK", 1: "RVE_EINVAL", 2: "RVE_ENOMEM", 3: "RVE_ECUDA", 4: "RVE_ENOCONV_LOCAL",
-                5: "RVE_ENOCONV_CG", 6: "RVE_ENOCONV_NEWTON", 7: "RVE_ENAN"}
+                5: "RVE_ENOCONV_CG", 6: "RVE_ENOCONV_NEWTON", 7: "RVE_ENAN", 8: "RVE_ETIMEOUT"}
 
 FIELDS = {"F": (0, 9), "P": (1, 9), "FP": (2, 9), "S": (3, 6), "SIGMA": (4, 9), "RHO_SSD": (5, 12),
           "RHO_GND": (6, 12), "RHO_GND18": (7, 18), "NYE": (8, 9), "VM": (9, 1), "TAUC": (10, 12),
@@ -77,6 +77,7 @@ _SIGS = {
     "rve_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "rve_get_tuning": (C.c_int, [C.c_void_p, C.c_void_p]),
     "rve_kernel_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rve_set_wait_limit": (C.c_int, [C.c_void_p, C.c_uint32]),
     "rve_project_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p]),
     "rve_sensitivity_bytes": (C.c_size_t, [C.c_void_p]),
@@ -345,6 +346,10 @@ class RVE:
         base = self.sens_workspace.data_ptr()
         aligned = (base + 255) // 256 * 256
         self._check(rve_sensitivity_enable(self.h, aligned, n, tol), "rve_sensitivity_enable")
+
+    def set_wait_limit(self, polls: int):
+        """Poll limit of the per-tile wait in the staged FP32 tangent apply (0: give up at once)."""
+        self._check(load_library().rve_set_wait_limit(self.h, int(polls)), "rve_set_wait_limit")
 
     def tuning(self):
         """Launch shapes in use: divergence grid cap, FFT fill target, staged FP32 apply, autotuned."""

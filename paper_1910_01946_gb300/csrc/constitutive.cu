@@ -126,12 +126,14 @@ __device__ void evaluate(const Consts& c, const double* S, const double* A, cons
   double Sn[6];
   cubic(c, E, Sn);
   double rn = 0.0;
+  bool fin = true;     // fmax drops a NaN operand: test every component
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     e.r[k] = S[k] - Sn[k];
     rn = fmax(rn, fabs(e.r[k]));
+    fin = fin && isfinite(e.r[k]);
   }
-  e.rn = isfinite(rn) ? rn : INFINITY;
+  e.rn = (fin && isfinite(rn)) ? rn : INFINITY;
 }
 
 // J = I - sum_a c^a (x) w^a with c^a = -dgp^a C : sym(Ce S0^a Minv)

@@ -438,7 +438,11 @@ rve_status cg_solve32(rve_s* h, const uint8_t* mask, double eta, int* iters, boo
     RVE_TRY(chunk == CG_CHUNK ? cg_chunk(h, mask, issue) : issue());
     issued += chunk;
     RVE_TRY(read_scalars(h));
-    if (h->hscal[DS_ERR] != 0.0) return fail(h, RVE_ECUDA, "a bounded wait for a staged copy gave up");
+    if (h->hscal[DS_ERR] != 0.0) {
+      // every block drained its copies before it left; the context is intact
+      RVE_CUDA(h, cudaMemsetAsync(h->dscal + DS_ERR, 0, sizeof(double), h->stream));
+      return fail(h, RVE_ETIMEOUT, "a bounded wait for a staged copy gave up");
+    }
     if (h->hscal[DS_DONE] != 0.0) break;
   }
   RVE_CUDA(h, launch_widen_x(h, h->stream));
@@ -540,7 +544,9 @@ rve_status sens_update(rve_s* h, const uint8_t* mask, double dt) {
     int it = 0;
     bool ok = false;
     if (h->opt.precision == 0 && h->opt.krylov != 1) RVE_TRY(cg_solve(h, mask, eta, &it, &ok));
-    if (!ok) RVE_TRY(bicgstab_solve(h, mask, std::fmax(eta, 1e-12), &it, &ok));
+    // an explicit tolerance is honoured as given; the default one is kept
+    // above what FP64 BiCGStab can reach
+    if (!ok) RVE_TRY(bicgstab_solve(h, mask, h->sens_tol > 0 ? eta : std::fmax(eta, 1e-12), &it, &ok));
     if (!ok) return fail(h, RVE_ENOCONV_CG, "the sensitivity solve did not converge");
     RVE_CUDA(h, launch_zero_means(h, h->x, 0x1FFu & ~kept_means(mask), h->stream));
     RVE_CUDA(h, launch_local_jvp(h, dt, 1, h->x, h->sd_Fp[sc][j], h->s_dtauc, h->s_dell, h->sd_rho[sc][j],
@@ -933,6 +939,7 @@ rve_status rve_step(rve_t* h, const double dFbar[9], const uint8_t strain_mask[9
     return st;
   };
   RVE_CUDA(h, cudaMemsetAsync(h->dcount + 8, 0, 4 * sizeof(int32_t), h->stream));
+  RVE_CUDA(h, cudaMemsetAsync(h->dscal + DS_ERR, 0, sizeof(double), h->stream));
   h->K_stale = false;
   rve_status st = run_hardening(h);
   if (st != RVE_OK) return finish(st);
@@ -954,8 +961,11 @@ rve_status rve_step(rve_t* h, const double dFbar[9], const uint8_t strain_mask[9
   loc.residuals[0] = res;
   for (;;) {
     loc.residual = res;
-    if (lfail) return finish(fail(h, RVE_ENOCONV_LOCAL, "local update did not converge"));
+    // a non-finite value anywhere in the state or the load path poisons the
+    // residual; it is reported as such even though the local update at the
+    // voxels concerned also fails
     if (!std::isfinite(res)) return finish(fail(h, RVE_ENAN, "non-finite residual"));
+    if (lfail) return finish(fail(h, RVE_ENOCONV_LOCAL, "local update did not converge"));
     if (res <= h->opt.newton_tol) break;
     if (loc.newton_iters >= h->opt.max_newton)
       return finish(fail(h, RVE_ENOCONV_NEWTON, "Newton-Raphson reached max_newton"));
@@ -1042,12 +1052,12 @@ rve_status rve_step(rve_t* h, const double dFbar[9], const uint8_t strain_mask[9
     ++loc.newton_iters;
     if (loc.newton_iters <= RVE_MAX_NEWTON_LOG) loc.residuals[loc.newton_iters] = res;
   }
-  loc.converged = 1;
   if (h->sens_on) {
     h->sens_valid = 0;
     st = sens_update(h, mask, dt);
     if (st != RVE_OK) return finish(st);      // nothing committed
   }
+  loc.converged = 1;
   if (cudaError_t e = launch_commit(h, h->stream)) {
     h->err = cudaGetErrorString(e);
     return finish(RVE_ECUDA);
@@ -1308,6 +1318,14 @@ rve_status rve_get_stress_sensitivity(rve_t* h, double dP[RVE_NTHETA * 9]) {
   if (!h || !dP) return RVE_EINVAL;
   if (!h->sens_on || !h->sens_valid) return fail(h, RVE_EINVAL, "no sensitivity of a converged increment");
   for (int k = 0; k < RVE_NTHETA * 9; ++k) dP[k] = h->sens_dP[k];
+  return RVE_OK;
+}
+
+rve_status rve_set_wait_limit(rve_t* h, uint32_t polls) {
+  if (!h) return RVE_EINVAL;
+  h->wait_polls = polls;
+  // captured CG chunks carry the old limit as a kernel argument
+  for (auto& g : h->graphs) release_graph(g);
   return RVE_OK;
 }
 

@@ -12,6 +12,7 @@
 #define RVE_MAX_RADIX_PASSES 12
 #define RVE_RED_BLOCKS 1216      // 152 SMs x 8: grid of the reducing kernels
 #define RVE_RED_THREADS 256
+#define RVE_WAIT_POLLS_DEFAULT (1u << 22)   // bounded mbarrier polls of the staged FP32 tangent apply
 
 struct FFTPlan {
   int n;                                  // transform length
@@ -129,6 +130,7 @@ struct rve_s {
   int fft_fill = 4 * 152;   // block count the FFT tile rules aim for
   bool autotuned = false;
   bool tma_apply = false;   // FP32 tangent apply staged by bulk copies (rve_options.tma)
+  unsigned wait_polls = RVE_WAIT_POLLS_DEFAULT;   // its per-tile wait limit (rve_set_wait_limit)
   // forward-mode sensitivities (rve_sensitivity_enable): state tangents
   // dFp (9) and d rho_SSD (12) per parameter, double-buffered so that a
   // failed increment leaves them untouched; scratch fields; d<P>/d theta of

@@ -174,7 +174,7 @@ constexpr int TA_ROWS = 81 + 9 + 9;              // K, r, p
 constexpr int TA_STAGE = TA_ROWS * TA_TV;        // floats per stage
 constexpr unsigned TA_STAGE_BYTES = TA_STAGE * sizeof(float);
 constexpr size_t TA_SMEM = 2 * (size_t)TA_STAGE_BYTES + 64;
-constexpr unsigned WAIT_LIMIT = 1u << 22;        // bounded mbarrier polls, then an error flag
+constexpr unsigned WAIT_LIMIT = RVE_WAIT_POLLS_DEFAULT;   // bounded mbarrier polls, then an error flag
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -202,9 +202,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
                : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
   return ok != 0;
 }
-// wait for the phase of the given parity; false after WAIT_LIMIT polls
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  for (unsigned i = 0; i < WAIT_LIMIT; ++i)
+// wait for the phase of the given parity; false after `limit` polls (0: gives
+// up without polling)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned limit = WAIT_LIMIT) {
+  for (unsigned i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -230,7 +231,8 @@ __global__ void __launch_bounds__(TA_TV, 1) k_tangent_apply32_tma(size_t nvox, c
                                                                  const float* __restrict__ r, float* __restrict__ p,
                                                                  float* __restrict__ t, double* __restrict__ ds,
                                                                  double* __restrict__ partial,
-                                                                 unsigned int* __restrict__ ticket) {
+                                                                 unsigned int* __restrict__ ticket,
+                                                                 unsigned tile_wait_polls) {
   extern __shared__ __align__(128) unsigned char ta_smem[];
   float* stage[2] = {reinterpret_cast<float*>(ta_smem), reinterpret_cast<float*>(ta_smem) + TA_STAGE};
   uint64_t* bar = reinterpret_cast<uint64_t*>(ta_smem + 2 * (size_t)TA_STAGE_BYTES);
@@ -245,15 +247,19 @@ __global__ void __launch_bounds__(TA_TV, 1) k_tangent_apply32_tma(size_t nvox, c
   }
   __syncthreads();
   long tile = blockIdx.x;
-  if (tile < ntiles) ta_issue(K, r, p, nvox, tile, stage[0], &bar[0]);
-  if (tile + gridDim.x < ntiles) ta_issue(K, r, p, nvox, tile + gridDim.x, stage[1], &bar[1]);
+  // pending[b]: stage b has copies in flight that no wait has seen land
+  bool pending[2] = {tile < ntiles, tile + gridDim.x < ntiles};
+  if (pending[0]) ta_issue(K, r, p, nvox, tile, stage[0], &bar[0]);
+  if (pending[1]) ta_issue(K, r, p, nvox, tile + gridDim.x, stage[1], &bar[1]);
   float acc = 0.0f;
   bool ok = true;
   unsigned phase[2] = {0u, 0u};
   for (int k = 0; tile < ntiles; tile += gridDim.x, ++k) {
     const int b = k & 1;
-    // the decision to go on is the whole block's: a barrier inside the loop follows
-    if (!__syncthreads_and(mbar_wait(&bar[b], phase[b]) ? 1 : 0)) { ok = false; break; }
+    // the decision to go on is the whole block's: a barrier inside the loop
+    // follows.  The per-tile wait gives up after tile_wait_polls polls.
+    if (!__syncthreads_and(mbar_wait(&bar[b], phase[b], tile_wait_polls) ? 1 : 0)) { ok = false; break; }
+    pending[b] = false;
     phase[b] ^= 1u;
     const size_t v = (size_t)tile * TA_TV + threadIdx.x;
     if (v < nvox) {
@@ -279,13 +285,16 @@ __global__ void __launch_bounds__(TA_TV, 1) k_tangent_apply32_tma(size_t nvox, c
     if (next < ntiles) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       ta_issue(K, r, p, nvox, next, stage[b], &bar[b]);
+      pending[b] = true;
     }
   }
   if (!ok) {
-    // a copy never completed: flag it, give both stages a bounded wait and leave
+    // a wait gave up: flag it, and before the block exits give every stage
+    // that still has copies in flight the full bounded wait, so that no copy
+    // lands in shared memory after the block has left
     if (threadIdx.x == 0) ds[DS_ERR] = 1.0;
-    mbar_wait(&bar[0], phase[0]);
-    mbar_wait(&bar[1], phase[1]);
+    if (pending[0]) mbar_wait(&bar[0], phase[0]);
+    if (pending[1]) mbar_wait(&bar[1], phase[1]);
   }
   const double s = blk_sum_v<float>(acc, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
@@ -636,7 +645,7 @@ cudaError_t launch_tangent_apply32(const rve_s* h, cudaStream_t s) {
     if (h->tma_apply)   // persistent: one block per SM
       k_tangent_apply32_tma<<<h->num_sms, TA_TV, TA_SMEM, s>>>(h->nvox, reinterpret_cast<const float*>(h->K[h->cur]),
                                                                h->r32, h->p32, h->t32, h->dscal, h->partial,
-                                                               (unsigned int*)(h->dcount + 4));
+                                                               (unsigned int*)(h->dcount + 4), h->wait_polls);
     else
       k_tangent_apply32<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, reinterpret_cast<const float*>(h->K[h->cur]),
                                                                    h->r32, h->p32, h->t32, h->dscal, h->partial,

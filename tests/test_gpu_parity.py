@@ -3,10 +3,13 @@ seeded inputs: each step of the increment on its own (projection, Nye curl and
 hardening, local update and tangent), whole increments on small RVEs, and
 sampled outputs on the 64^3 / 100-grain workload the benchmark times.
 
-Tolerance: the fields are compared as max|gpu - oracle| / max|oracle| per
-field.  Single kernels agree to round-off (1e-12); whole increments to the
-spec bound 1e-9 (both sides converge the same discrete equations to a
-relative residual of 1e-11, so their difference is the conditioning times
+Tolerance.  Single kernels are compared as max|gpu - oracle| / max|oracle|
+per field and agree to round-off (1e-11 .. 1e-13).  Whole increments are
+compared per component on the informative part of each field (F - I, Fp - I,
+rho_SSD - rho_0, P, sigma, rho_GND): max|gpu - oracle| over the component's
+own max|oracle|, floored at 1e-3 of the field's largest component, against
+the 1e-9 relative bound (both sides converge the same discrete equations to
+a relative residual of 1e-11, so their difference is the conditioning times
 that residual plus round-off)."""
 import numpy as np
 import pytest
@@ -36,6 +39,41 @@ def pkg():
 
 def relerr(a, b):
     return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+
+EYE9 = np.eye(3).reshape(9)
+
+
+def comp_err(g, o, base=None):
+    """Largest per-component relative error of field g against o (last axis =
+    components) after subtracting `base` from both (the part that carries
+    the information: F - I, Fp - I, rho - rho_0)."""
+    g = np.asarray(g, dtype=np.float64)
+    o = np.asarray(o, dtype=np.float64)
+    nc = o.shape[-1]
+    g = g.reshape(-1, nc)
+    o = o.reshape(-1, nc)
+    if base is not None:
+        g = g - base
+        o = o - base
+    scale = np.abs(o).max(axis=0)
+    den = np.maximum(scale, 1e-3 * scale.max())
+    return float((np.abs(g - o).max(axis=0) / den).max())
+
+
+def check_increment_fields(g, o, tol=1e-9):
+    shape = g.shape
+    rho0 = o.mat.rho0_total / 12
+    assert comp_err(g.field("F"), to_field(o.F, shape), EYE9) < tol, "F - I"
+    assert comp_err(g.field("FP"), to_field(o.Fp, shape), EYE9) < tol, "Fp - I"
+    assert comp_err(g.field("P"), to_field(o.P, shape)) < tol, "P"
+    sig = o.P @ np.swapaxes(o.F, 1, 2) / np.linalg.det(o.F)[:, None, None]
+    assert comp_err(g.field("SIGMA"), to_field(sig, shape)) < tol, "sigma"
+    assert comp_err(g.field("RHO_SSD"), o.rho_ssd.reshape(shape + (12,)), rho0) < tol, "rho_SSD - rho_0"
+    assert comp_err(g.field("RHO_GND"), o.rho_gnd.reshape(shape + (12,))) < tol, "rho_GND"
+    Pg, sg = g.macro_stress()
+    Po, so = o.macro_stress()
+    assert relerr(Pg, Po) < tol and relerr(sg, so) < tol
 
 
 def to_field(a, shape):
@@ -123,30 +161,40 @@ def run_both(pkg, wl, n_inc, gpu_opts=None):
                          ids=["cu8x4", "al12x3"])
 def test_increments_match_oracle(pkg, wl):
     g, o, curve = run_both(pkg, wl, wl.increments)
-    shape = g.shape
-    tol = 1e-9
-    assert relerr(g.field("F"), to_field(o.F, shape)) < tol
-    assert relerr(g.field("P"), to_field(o.P, shape)) < tol
-    assert relerr(g.field("FP"), to_field(o.Fp, shape)) < tol
-    assert relerr(g.field("RHO_SSD"), o.rho_ssd.reshape(shape + (12,))) < tol
-    assert relerr(g.field("RHO_GND"), o.rho_gnd.reshape(shape + (12,))) < tol
-    Pg, sg = g.macro_stress()
-    Po, so = o.macro_stress()
-    assert relerr(Pg, Po) < tol and relerr(sg, so) < tol
+    check_increment_fields(g, o)
     for a, b in curve:
-        assert abs(a - b) < tol * abs(b)
-    assert o.rho_gnd.max() > 0
+        assert abs(a - b) < 1e-9 * abs(b)
+    assert o.rho_gnd.max() > 0 and np.abs(o.Fp - np.eye(3)).max() > 1e-4
     g.close()
 
 
 def test_cu16_first_increments_match_oracle(pkg):
     wl = rvegen.WORKLOADS["cu16"]
     g, o, curve = run_both(pkg, wl, 3)
-    shape = g.shape
-    for name, ref in (("F", to_field(o.F, shape)), ("P", to_field(o.P, shape)), ("FP", to_field(o.Fp, shape))):
-        assert relerr(g.field(name), ref) < 1e-9, name
-    assert relerr(g.field("RHO_GND"), o.rho_gnd.reshape(shape + (12,))) < 1e-9
-    assert relerr(g.field("SIGMA"), (o.P @ np.swapaxes(o.F, 1, 2) / np.linalg.det(o.F)[:, None, None]).reshape(shape + (9,))) < 1e-9
+    check_increment_fields(g, o)
+    g.close()
+
+
+@pytest.mark.parametrize("shape", [(24, 24, 6), (6, 24, 24)], ids=["24x24x6", "6x24x24"])
+def test_increments_match_oracle_mixed_radix_grid(pkg, shape):
+    """Grids whose FFT plans chain radix-4, radix-2 and radix-3 passes
+    (24 = 4 * 2 * 3), on the x and y axes or on the y and z axes: the plan
+    family of the 48^3 and 96^3 sweep RVEs.  Three increments to 6e-4 (past
+    the plastic onset, GND active)."""
+    n0, n1, n2 = shape
+    ng = 6
+    gid, _ = rvegen.voronoi_grain_map(0, ng, 2401, shape=shape)
+    quat = rvegen.random_quaternions(ng, 2401 + 7919)
+    mat = rvegen.material("Cu")
+    L = 20e-6 * (np.pi * ng / 6.0) ** (1.0 / 3.0)
+    g = pkg.RVE(gid, quat, mat, L)
+    o = solver.RVE(gid, quat, mat, L)
+    d = np.zeros(9); d[0] = 2e-4
+    for k in range(3):
+        assert g.step(d, MASK, np.zeros(9), 0.2)["converged"]
+        assert o.step(d, MASK, np.zeros(9), 0.2).converged
+    check_increment_fields(g, o)
+    assert o.rho_gnd.max() > 0 and np.abs(o.Fp - np.eye(3)).max() > 5e-4
     g.close()
 
 
@@ -177,14 +225,18 @@ def test_failed_step_leaves_state_and_handle_usable(pkg):
     g.close()
 
 
-def test_full_size_workload_sampled(pkg):
-    """64^3, 100 grains, Cu (the benchmark workload), two increments on the GPU;
-    the oracle recomputes the local update at sampled voxels from the GPU's
-    state and checks the equilibrium and macro invariants on the full field."""
+@pytest.mark.parametrize("n_inc", [2, 12])
+def test_full_size_workload_sampled(pkg, n_inc):
+    """64^3, 100 grains, Cu (the benchmark workload, in the launch
+    configuration the benchmark times), 2 or 12 increments (0.2 % and 1.2 %
+    strain, the second well into plastic flow) on the GPU; the oracle
+    recomputes the hardening on the full field and the local update and
+    tangent at sampled voxels from the GPU's state, and checks the
+    equilibrium and macro invariants on the full field."""
     wl = rvegen.WORKLOADS["cu64"]
     gid, quat, mat = wl.inputs()
     g = pkg.RVE(gid, quat, mat, wl.edge)
-    for k in range(2):
+    for k in range(n_inc):
         info = g.step(wl.dFbar(), MASK, np.zeros(9), wl.dt)
         assert info["converged"]
     o = solver.RVE(gid, quat, mat, wl.edge)
@@ -193,7 +245,7 @@ def test_full_size_workload_sampled(pkg):
     P = g.field("P").reshape(nv, 3, 3)
     # macro invariants
     Fm = F.mean(axis=0).reshape(9)
-    assert np.allclose(Fm[MASK == 1], (np.eye(3).reshape(9) + 2 * wl.dFbar())[MASK == 1], atol=1e-14)
+    assert np.allclose(Fm[MASK == 1], (np.eye(3).reshape(9) + n_inc * wl.dFbar())[MASK == 1], atol=1e-14)
     Pm = P.mean(axis=0).reshape(9)
     assert np.abs(Pm[MASK == 0]).max() < 1e-9 * np.abs(Pm).max()
     R = sp.project(P.reshape(gid.shape + (3, 3)), MASK, o.h)
@@ -230,11 +282,7 @@ def test_mixed_precision_increments_match_oracle(pkg, wl):
     """precision = 1: FP32 conjugate gradients, FP64 local update and residual.
     Newton converges the FP64 residual, so the increment is the FP64 one."""
     g, o, curve = run_both(pkg, wl, wl.increments, gpu_opts=dict(precision=1))
-    shape = g.shape
-    for name, ref in (("F", to_field(o.F, shape)), ("P", to_field(o.P, shape)), ("FP", to_field(o.Fp, shape))):
-        assert relerr(g.field(name), ref) < 1e-9, name
-    assert relerr(g.field("RHO_SSD"), o.rho_ssd.reshape(shape + (12,))) < 1e-9
-    assert relerr(g.field("RHO_GND"), o.rho_gnd.reshape(shape + (12,))) < 1e-9
+    check_increment_fields(g, o)
     assert g.field("TANGENT").dtype == np.float64
     g.close()
 
@@ -247,8 +295,8 @@ def test_mixed_precision_matches_fp64_path_cu16(pkg):
     for k in range(4):
         ia = a.step(wl.dFbar(), MASK, np.zeros(9), wl.dt)
         ib = b.step(wl.dFbar(), MASK, np.zeros(9), wl.dt)
-    for name in ("F", "P", "FP", "RHO_GND", "SIGMA"):
-        assert relerr(b.field(name), a.field(name)) < 1e-9, name
+    for name, base in (("F", EYE9), ("P", None), ("FP", EYE9), ("RHO_GND", None), ("SIGMA", None)):
+        assert comp_err(b.field(name), a.field(name), base) < 1e-9, name
     assert relerr(b.macro_stress()[0], a.macro_stress()[0]) < 1e-9
     a.close(); b.close()
 
@@ -266,10 +314,7 @@ def test_bicgstab_increments_match_oracle(pkg, wl, precision):
         oi = o.step(wl.dFbar(), MASK, np.zeros(9), wl.dt)
         assert gi["converged"] and oi.converged
         assert gi["bicgstab_solves"] == gi["newton_iters"]
-    shape = g.shape
-    for name, ref in (("F", to_field(o.F, shape)), ("P", to_field(o.P, shape)), ("FP", to_field(o.Fp, shape))):
-        assert relerr(g.field(name), ref) < 1e-9, name
-    assert relerr(g.field("RHO_GND"), o.rho_gnd.reshape(shape + (12,))) < 1e-9
+    check_increment_fields(g, o)
     g.close()
 
 
@@ -284,6 +329,6 @@ def test_staged_tangent_apply_matches_plain_loads(pkg):
     for k in range(3):
         assert a.step(wl.dFbar(), MASK, np.zeros(9), wl.dt)["converged"]
         assert b.step(wl.dFbar(), MASK, np.zeros(9), wl.dt)["converged"]
-    for name in ("F", "P", "FP", "RHO_GND"):
-        assert relerr(a.field(name), b.field(name)) < 1e-9, name
+    for name, base in (("F", EYE9), ("P", None), ("FP", EYE9), ("RHO_GND", None)):
+        assert comp_err(a.field(name), b.field(name), base) < 1e-9, name
     a.close(); b.close()
