@@ -12,7 +12,9 @@ voxel-iterations/s = voxels x conjugate-gradient mat-vecs / time.
 With N > 1 (torchrun, one rank per GPU) every rank runs an independent
 replica (the increment does not shard); value = all ranks' voxel-iterations /
 max-over-ranks time.  --impl reference times the FP64 CPU oracle on the same
-workload (a bounded sample per step, see oracle_sample()).
+workload (a timed slice of its increment per step, see oracle_slice(); with
+--full every step is one whole oracle increment).  --fft-compare times the
+hand-written FFT against cuFFT.
 """
 from __future__ import annotations
 
@@ -35,13 +37,15 @@ import rvegen  # noqa: E402
 
 WORKLOAD = "cu64"
 FP64_PEAK_GFLOPS = 152 * 4 * 2.070   # 152 SMs x 2 DFMA (4 flop) per clock x 2.07 GHz = 1258.6
-# per-increment counts of the GPU path on this workload (local evaluations,
-# CG iterations), used to compose the CPU oracle's time per increment
-REF_EVALS_PER_INC = 6.0
-REF_CG_PER_INC = 500.0
+# The oracle's own mix of work on the 64^3 / 100-grain workload: conjugate-
+# gradient iterations per local evaluation (local update with tangent on
+# every voxel), from full oracle increments of that workload.  A timed slice
+# of the oracle keeps this mix, so that its voxel-iterations/s is the one its
+# whole increments reach.
+ORACLE_CG_PER_EVAL = 250.0
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=47)
@@ -59,7 +63,11 @@ def parse():
                     help="sweep: the 16-RVE grain-size sweep stepped together (rve_step_batch)")
     ap.add_argument("--precision", default="f64", choices=["f64", "mixed"],
                     help="mixed: FP32 conjugate gradients with FP64 local update and residual")
-    return ap.parse_args()
+    ap.add_argument("--full", action="store_true",
+                    help="with --impl reference: every step is one whole oracle increment (no slice)")
+    ap.add_argument("--fft-compare", action="store_true",
+                    help="time the hand-written FFT against cuFFT (3 and 9 fields, 64^3 and 128^3, FP64 and FP32)")
+    return ap.parse_args(argv)
 
 
 # ---------------------------------------------------------------- clocks
@@ -126,23 +134,39 @@ CONST_BYTES = 364 + 216        # reads F, dF, Fp^-1, tauc, S, grain; writes S, d
 TANGENT_BYTES = 364 + 648      # reads F, dF, Fp^-1, tauc, S, grain; writes K
 
 
-def kernel_models(n0, n1, n2, local=None):
-    """Algorithmic FP64 flops and bytes per launch of each kernel category
-    (FFTs: 2.5 N log2 N per real and 5 N log2 N per complex transform).
-    `local` = (launches, local iterations, local evaluations) of the local
-    update in the timed region, for its per-launch average."""
+def fft_models(n0, n1, n2, nf):
+    """Algorithmic FP64 flops and bytes of one launch of each FFT pass over nf
+    real fields (2.5 N log2 N per real and 5 N log2 N per complex transform;
+    6 flops per spectrum value for the operator between the z passes)."""
     nvox = n0 * n1 * n2
     nkx = n0 // 2 + 1
     nspec = nkx * n1 * n2
     lg = math.log2
-    fx = 9 * n2 * n1 * 2.5 * n0 * lg(n0)
-    fy = 9 * n2 * nkx * 5.0 * n1 * lg(n1)
-    fz = 9 * nkx * n1 * 2 * 5.0 * n2 * lg(n2) + 9 * nspec * 6.0
+    fx = nf * n2 * n1 * 2.5 * n0 * lg(n0)
+    fy = nf * n2 * nkx * 5.0 * n1 * lg(n1)
+    fz = nf * nkx * n1 * 2 * 5.0 * n2 * lg(n2) + nf * nspec * 6.0
+    return {"x": (fx, nf * nvox * 8 + nf * nspec * 16), "y": (fy, 2 * nf * nspec * 16),
+            "z": (fz, 2 * nf * nspec * 16)}
+
+
+def kernel_models(n0, n1, n2, local=None):
+    """Algorithmic FP64 flops and bytes per launch of each kernel category.
+    The fft_* categories count the three-field transforms of the projection
+    (the CG loop, the residual); fft_curl counts all five passes of the
+    nine-field Nye-curl transform, so its per-launch figure is a fifth of one
+    curl.  `local` = (launches, local iterations, local evaluations) of the
+    local update in the timed region, for its per-launch average."""
+    nvox = n0 * n1 * n2
+    f3 = fft_models(n0, n1, n2, 3)
+    f9 = fft_models(n0, n1, n2, 9)
+    # one curl = x, y, z (with the operator), y^-1, x^-1 passes over nine fields
+    curl = [(2 * f9["x"][i] + 2 * f9["y"][i] + f9["z"][i]) / 5 for i in (0, 1)]
     return {
-        "fft_x_r2c": (fx, 9 * nvox * 8 + 9 * nspec * 16),
-        "fft_y": (fy, 2 * 9 * nspec * 16),
-        "fft_z_op": (fz, 2 * 9 * nspec * 16),
-        "fft_x_c2r": (fx, 9 * nvox * 8 + 9 * nspec * 16),
+        "fft_x_r2c": f3["x"],
+        "fft_y": f3["y"],
+        "fft_z_op": f3["z"],
+        "fft_x_c2r": f3["x"],
+        "fft_curl": (curl[0], curl[1]),
         "tangent_apply": (nvox * (162 + 18 + 18), nvox * (81 + 9 + 9 + 9 + 9) * 8),
         # tiled divergence 9 -> 3 fields: per field a z-pair sum and 3 corner-sum
         # additions, 2 row additions per row, and the means of the stress-
@@ -162,37 +186,111 @@ def kernel_models(n0, n1, n2, local=None):
 FP32_CG = ("tangent_apply", "stencil", "cg_update", "fft_x_r2c", "fft_y", "fft_z_op", "fft_x_c2r")
 
 
-def roofline(stats, shape, peaks, local=None, prec=0):
+
+def rate(flops, nbytes, avg_s, peaks):
+    """The bound of one launch (FP64 ALU or HBM, whichever needs more time at
+    the peaks) and its achieved fraction of that bound."""
+    t_alu = flops / (FP64_PEAK_GFLOPS * 1e9)
+    t_hbm = nbytes / (peaks["hbm_gbs"] * 1e9)
+    if t_alu >= t_hbm:
+        ach = flops / avg_s / 1e9
+        return dict(bound="alu", achieved=ach, peak=FP64_PEAK_GFLOPS, unit="GFLOP/s (FP64)",
+                    frac=ach / FP64_PEAK_GFLOPS)
+    ach = nbytes / avg_s / 1e9
+    return dict(bound="hbm", achieved=ach, peak=peaks["hbm_gbs"], unit="GB/s", frac=ach / peaks["hbm_gbs"])
+
+
+def roofline_all(stats, shape, peaks, local=None, prec=0):
+    """Every timed category: launches, average launch time, share of kernel
+    time, and its roofline fraction (algorithmic figures per launch over the
+    event-timed average launch duration)."""
     models = kernel_models(*shape, local=local)
     if prec == 1:
         for k in FP32_CG:
             models[k] = (0.0, models[k][1] / 2)
     timed = {k: v for k, v in stats.items() if v[0] > 0 and v[1] > 0}
-    if not timed:
+    total = sum(v[1] for v in timed.values())
+    out = {}
+    for k, (n, ms) in timed.items():
+        avg_s = ms / n / 1e3
+        e = {"launches": n, "avg_us": avg_s * 1e6, "share": ms / total}
+        if k in models:
+            flops, nbytes = models[k]
+            e.update(rate(flops, nbytes, avg_s, peaks))
+            e["algorithmic_flops"] = flops
+            e["algorithmic_bytes"] = nbytes
+        out[k] = e
+    return out
+
+
+def roofline(stats, shape, peaks, local=None, prec=0):
+    """(dominant category by event time, its entry of roofline_all)."""
+    allr = roofline_all(stats, shape, peaks, local=local, prec=prec)
+    if not allr:
         return None, None
-    dom = max(timed, key=lambda k: timed[k][1])
-    n, ms = timed[dom]
-    avg_s = ms / n / 1e3
-    out = {"kernel": dom, "launches": n, "avg_us": avg_s * 1e6, "share": ms / sum(v[1] for v in timed.values())}
-    if dom in models:
-        flops, nbytes = models[dom]
-        t_alu = flops / (FP64_PEAK_GFLOPS * 1e9)
-        t_hbm = nbytes / (peaks["hbm_gbs"] * 1e9)
-        if t_alu >= t_hbm:
-            ach = flops / avg_s / 1e9
-            out.update(bound="alu", achieved=ach, peak=FP64_PEAK_GFLOPS, unit="GFLOP/s (FP64)", frac=ach / FP64_PEAK_GFLOPS)
-        else:
-            ach = nbytes / avg_s / 1e9
-            out.update(bound="hbm", achieved=ach, peak=peaks["hbm_gbs"], unit="GB/s", frac=ach / peaks["hbm_gbs"])
-        out["algorithmic_flops"] = flops
-        out["algorithmic_bytes"] = nbytes
-    return dom, out
+    dom = max(allr, key=lambda k: allr[k]["share"])
+    return dom, allr[dom]
+
+
+def measured_fp64_peak(smi_index):
+    """The device's FP64 FMA rate, timed live (libbench_aux: chains of
+    independent DFMA, 4 blocks of 256 threads per SM, best of 10 launches of
+    about 20 ms), with the SM clock sampled meanwhile."""
+    import ctypes
+    from paper_1910_01946_gb300 import _build
+    try:
+        lib = ctypes.CDLL(_build.build_aux())
+    except (OSError, RuntimeError):
+        return None
+    lib.aux_fp64_peak.restype = ctypes.c_int
+    lib.aux_fp64_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double)]
+    clocks = ClockSampler(smi_index)
+    clocks.start()
+    time.sleep(0.25)
+    g, ms = ctypes.c_double(), ctypes.c_double()
+    rc = lib.aux_fp64_peak(4, 8000, 10, ctypes.byref(g), ctypes.byref(ms))
+    time.sleep(0.1)
+    clocks.stop()
+    if rc != 0:
+        return None
+    c = clocks.summary()
+    return {"gflops": g.value, "launch_ms": ms.value, "sm_mhz": c["sm_mhz"], "samples": c["samples"],
+            "how": "DFMA chains, 8 per thread, 4 x 256 threads per SM, best of 10 launches (libbench_aux)"}
+
+
+def mixed_accuracy(pkg, rve, wl, gid, quat, mat, dev, a, P_hist):
+    """The mixed-precision run against the FP64 path on the same increments:
+    an FP64 handle steps through the warm-up and timed increments; the
+    largest relative error of the macroscopic stress <P> over the timed
+    increments, and of the per-voxel Cauchy stress and GND densities of the
+    last increment (max |mixed - fp64| / max |fp64| over the field)."""
+    mask = rvegen.UNIAXIAL_X_MASK
+    ref = pkg.RVE(gid, quat, mat, wl.edge, device=dev, precision=0, own_stream=True, graphs=a.graphs)
+    try:
+        for _ in range(a.warmup):
+            ref.step(wl.dFbar(), mask, np.zeros(9), wl.dt)
+        perr = 0.0
+        for k in range(a.steps):
+            ref.step(wl.dFbar(), mask, np.zeros(9), wl.dt)
+            Pr = ref.macro_stress()[0]
+            perr = max(perr, float(np.abs(P_hist[k] - Pr).max() / np.abs(Pr).max()))
+        out = {"macro_P_rel_err_max": perr}
+        for name in ("SIGMA", "RHO_GND"):
+            f, r = rve.field(name), ref.field(name)
+            out[f"{name.lower()}_rel_err_max"] = float(np.abs(f - r).max() / np.abs(r).max())
+        out["how"] = (f"FP64 handle stepped through the same {a.warmup} + {a.steps} increments; <P> compared at "
+                      "every timed increment, sigma and rho_GND fields at the last")
+        return out
+    finally:
+        ref.close()
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # kernels that lead the timed region, from one ncu capture of the 64^3
 # workload; keyed by (category, precision).  Kernels changed since that
 # capture have no entry (reported as null), as do other grid sizes.
+TRAFFIC_SOURCE = "profiles/kernels_cu64.md"
 TRAFFIC_64 = {
     ("tangent_apply", 0): 207.66e6 + 5.10e6,   # K : p reads its algorithmic 207.6 MB
     ("tangent_apply", 1): 103.84e6 + 3.53e6,   # TMA-staged FP32 apply (float K, r, p)
@@ -213,47 +311,72 @@ def load_peaks():
 
 
 # ---------------------------------------------------------------- CPU oracle
-def oracle_sample(wl, frac=0.08, n_cg=2, seed=0):
-    """Bounded sample of the FP64 CPU oracle on the workload: the local update
-    with tangent on a seeded subset of grains holding about `frac` of the
-    voxels, and n_cg conjugate-gradient iterations on the full grid.  Returns
-    the composed seconds per increment for REF_EVALS_PER_INC local
-    evaluations and REF_CG_PER_INC CG iterations, and the sample's own CPU
-    seconds."""
+def oracle_slice(wl, n_cg, seed=0):
+    """A bounded slice of the FP64 CPU oracle's increment on the full
+    workload, timed for real (wall clock on the host cores): the local update
+    with tangent on a seeded subset of grains holding n_cg / ORACLE_CG_PER_EVAL
+    of the voxels, then n_cg conjugate-gradient iterations on the full grid
+    (the tangent field tiled from the subset).  The slice keeps the oracle's
+    own mix of the two, so its rate nvox * n_cg / seconds is the
+    voxel-iterations/s of the oracle's whole increments.  The hardening (once
+    per increment) is set up before the clock starts.  Returns (seconds,
+    voxels evaluated, n_cg)."""
     from oracle import solver
     from oracle import spectral as sp
     gid, quat, mat = wl.inputs()
     o = solver.RVE(gid, quat, mat, wl.edge)
     nv = gid.size
-    t0 = time.perf_counter()
     tauc, ell = o.hardening()
-    t_hard = time.perf_counter() - t0
     F = o.F + (wl.dFbar() * rvegen.UNIAXIAL_X_MASK).reshape(3, 3)
     rng = np.random.default_rng(seed)
-    order = rng.permutation(len(o.grains))
+    target = nv * n_cg / ORACLE_CG_PER_EVAL
     chosen, count = [], 0
-    for gi in order:
+    for gi in rng.permutation(len(o.grains)):
+        if count >= target:
+            break
         chosen.append(o.grains[gi])
         count += len(o.grains[gi]["idx"])
-        if count >= frac * nv:
-            break
     keep = o.grains
     o.grains = chosen
     idx = np.concatenate([g["idx"] for g in chosen])
-    t0 = time.perf_counter()
-    P, K, S, M, dg, lit, lf = o.constitutive(F, tauc, o.S, wl.dt)
-    t_eval = (time.perf_counter() - t0) / len(idx)
-    o.grains = keep
-    Kfull = np.resize(K[idx], (nv, 3, 3, 3, 3))
-    R = o.flat(sp.project(o.field(np.resize(P[idx], (nv, 3, 3))), rvegen.UNIAXIAL_X_MASK, o.h))
     o.opts.max_cg = n_cg
     o.opts.cg_tol = 1e-300
     t0 = time.perf_counter()
+    P, K, S, M, dg, lit, lf = o.constitutive(F, tauc, o.S, wl.dt)
+    o.grains = keep
+    Kfull = np.resize(K[idx], (nv, 3, 3, 3, 3))
+    R = o.flat(sp.project(o.field(np.resize(P[idx], (nv, 3, 3))), rvegen.UNIAXIAL_X_MASK, o.h))
     o.cg(Kfull, -R, rvegen.UNIAXIAL_X_MASK)
-    t_cg = (time.perf_counter() - t0) / n_cg
-    per_inc = REF_EVALS_PER_INC * nv * t_eval + REF_CG_PER_INC * t_cg + t_hard
-    sample_s = t_hard + t_eval * len(idx) + t_cg * n_cg
-    return per_inc, sample_s, len(idx), t_eval, t_cg
+    return time.perf_counter() - t0, len(idx), n_cg
+
+
+def oracle_increments(wl, warmup, steps):
+    """Whole increments of the FP64 CPU oracle, each timed for real: `warmup`
+    untimed increments, then `steps` timed ones.  Returns (seconds of each
+    timed increment, CG iterations of each, local evaluations of each)."""
+    from oracle import solver
+    gid, quat, mat = wl.inputs()
+    o = solver.RVE(gid, quat, mat, wl.edge)
+    n_eval = [0]
+    evaluate = o.constitutive
+
+    def counted(*args, **kw):
+        n_eval[0] += 1
+        return evaluate(*args, **kw)
+    o.constitutive = counted
+    secs, cgs, evals = [], [], []
+    for k in range(warmup + steps):
+        n_eval[0] = 0
+        t0 = time.perf_counter()
+        info = o.step(wl.dFbar(), rvegen.UNIAXIAL_X_MASK, np.zeros(9), wl.dt)
+        el = time.perf_counter() - t0
+        if not info.converged:
+            raise RuntimeError(f"oracle increment {k} did not converge")
+        if k >= warmup:
+            secs.append(el)
+            cgs.append(int(sum(info.cg_iters)))
+            evals.append(n_eval[0])
+    return secs, cgs, evals
 
 
 def reduce_over_ranks(ms, units, device="cpu"):
@@ -393,8 +516,59 @@ def run_sweep(a):
     print(json.dumps(line))
 
 
+def run_fft_compare(a):
+    """The hand-written batched 3-D real FFT against cuFFT on the same box:
+    forward + inverse of 3 and 9 fields at 64^3 and 128^3, FP64 and FP32
+    (the library's FP32 transform exists for 3 fields, the mixed-precision
+    conjugate gradients).  Ours runs on a handle's own buffers with the
+    operator that sits between its z passes (the inverse-Laplacian weight for
+    3 fields, the Galerkin projection for 9); cuFFT runs plain D2Z + Z2D
+    (R2C + C2R) plans.  CUDA-event device time per forward + inverse pair."""
+    import ctypes
+    import torch
+    import paper_1910_01946_gb300 as pkg
+    from paper_1910_01946_gb300 import _build
+    _build.build()
+    pkg.load_library()
+    aux = ctypes.CDLL(_build.build_aux())
+    aux.aux_cufft_time.restype = ctypes.c_int
+    aux.aux_cufft_time.argtypes = [ctypes.c_int] * 6 + [ctypes.POINTER(ctypes.c_double)]
+    rows = []
+    clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    clocks.start()
+    for n in (64, 128):
+        reps = 50 if n == 64 else 20
+        gid = np.zeros((n, n, n), dtype=np.int32)
+        quat = np.array([[1.0, 0.0, 0.0, 0.0]])
+        mat = rvegen.material("Cu")
+        for prec in (0, 1):
+            r = pkg.RVE(gid, quat, mat, 20e-6, own_stream=True, precision=prec)
+            for nf in (3, 9):
+                fp32 = prec == 1
+                ours = r.time_fft(nf, fp32=fp32, reps=reps) if (nf == 3 or not fp32) else None
+                ms = ctypes.c_double()
+                rc = aux.aux_cufft_time(n, n, n, nf, int(fp32), reps, ctypes.byref(ms))
+                cu = ms.value if rc == 0 else None
+                rows.append({"grid": f"{n}^3", "fields": nf, "dtype": "f32" if fp32 else "f64",
+                             "ours_us": None if ours is None else round(1e3 * ours, 2),
+                             "cufft_us": None if cu is None else round(1e3 * cu, 2),
+                             "ours_over_cufft": None if (ours is None or cu is None) else round(ours / cu, 3)})
+            r.close()
+            del r
+            torch.cuda.empty_cache()
+    clocks.stop()
+    line = {"metric": "3-D real FFT forward + inverse, hand-written vs cuFFT", "unit": "us per pair",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic (zeros; FFT time does not depend on values)",
+            "rows": rows, "clocks": clocks.summary(),
+            "note": "ours includes the operator fused between the z passes; cuFFT is a comparison only "
+                    "(libbench_aux.so), not linked into librve.so"}
+    print(json.dumps(line))
+
+
 def main():
     a = parse()
+    if a.fft_compare:
+        return run_fft_compare(a)
     if a.workload == "sweep":
         return run_sweep(a)
     if a.sensitivity:
@@ -413,24 +587,38 @@ def main():
     if a.impl == "reference":
         if world > 1 and rank != 0:
             return
-        times = []
-        samp = None
-        for k in range(a.warmup + a.steps):
-            per_inc, sample_s, nsub, t_eval, t_cg = oracle_sample(wl, frac=0.02, n_cg=1, seed=k)
-            if k >= a.warmup:
-                times.append(per_inc)
-                samp = (sample_s, nsub)
-        ms = 1e3 * statistics.mean(times)
-        value = nvox * REF_CG_PER_INC / (ms / 1e3)
+        if a.full:
+            secs, cgs, evals = oracle_increments(wl, a.warmup, a.steps)
+            el = sum(secs)
+            value = nvox * sum(cgs) / el
+            sample = (f"{a.steps} whole oracle increments (after {a.warmup} untimed), each timed: "
+                      f"{sum(cgs) / a.steps:.0f} CG iterations and {sum(evals) / a.steps:.1f} local "
+                      f"evaluations per increment, {el / a.steps:.1f} s per increment")
+            ms = 1e3 * el / a.steps
+        else:
+            # every step a real slice of 3 CG iterations and its share of the
+            # local update (about 3 s on 16 cores at 64^3), warm-up slices untimed
+            n_cg = 3
+            secs = []
+            for k in range(a.warmup + a.steps):
+                t, nsub, _ = oracle_slice(wl, n_cg, seed=k)
+                if k >= a.warmup:
+                    secs.append(t)
+            el = sum(secs)
+            value = nvox * n_cg * a.steps / el
+            ms = 1e3 * el / a.steps
+            sample = (f"per step: a timed slice of the oracle's increment on the full grid, {n_cg} CG "
+                      f"iterations and the local update with tangent on about {nsub} voxels (the oracle's "
+                      f"own mix of {ORACLE_CG_PER_EVAL:g} CG iterations per local evaluation)")
         line = {"impl": "reference", "metric": "voxel-iterations/s", "value": value, "unit": "voxel-iter/s",
                 "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
                 "cpu_baseline": {"value": value, "unit": "voxel-iter/s", "cores": cpu_cores(), "kind": "oracle",
-                                 "sample": f"per step: oracle local update + tangent on {samp[1]} voxels and 1 CG "
-                                           f"iteration on the full grid ({samp[0]:.1f} s), composed to "
-                                           f"{REF_EVALS_PER_INC:g} evaluations + {REF_CG_PER_INC:g} CG iterations "
-                                           "per increment"},
+                                 "sample": sample},
                 "e2e": {"value": value, "unit": "voxel-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        if a.full:
+            line["detail"] = {"seconds_per_increment": secs, "cg_iters": cgs, "local_evals": evals,
+                              "cg_iters_per_local_eval": sum(cgs) / max(1, sum(evals))}
         print(json.dumps(line))
         return
 
@@ -482,8 +670,11 @@ def main():
     ev0.record(stream)
     cg_total, newton_total, evals = 0, 0, 0
     local_iters, local_evals = 0, 0
+    P_hist = []
     for _ in range(a.steps):
         info = rve.step(wl.dFbar(), mask, Pbar, wl.dt)
+        if prec == 1:
+            P_hist.append(rve.macro_stress()[0])     # host read after the step's own synchronisation
         cg_total += info["cg_iters_total"]
         newton_total += info["newton_iters"]
         local_iters += info["local_iters_total"]
@@ -502,13 +693,20 @@ def main():
     stats = rve.kernel_stats()
     rve.profile(False)
     evals = stats["constitutive"][0]
+    # per-kernel events cost the replay time between kernels; the ratio says by
+    # how much the summed event times exceed the plain timed region
+    replay_over_timed = sum(v[1] for v in stats.values()) / ms if ms > 0 else None
     ms_max, cg_all = reduce_over_ranks(ms, cg_total, device=dev)
     value = nvox * cg_all / (ms_max / 1e3)
     launches = launches_timed
     shapes = rve.tuning()
+    accuracy = None
+    if prec == 1 and rank == 0:
+        accuracy = mixed_accuracy(pkg, rve, wl, gid, quat, mat, dev, a, P_hist)
     rve.close()
     del rve
     torch.cuda.empty_cache()
+    fp64_peak = measured_fp64_peak(smi_index) if rank == 0 else None
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -550,26 +748,31 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return
-    dom, roof = roofline(stats, (wl.n, wl.n, wl.n), peaks, local=(evals, local_iters, local_evals), prec=prec)
+    loc = (evals, local_iters, local_evals)
+    by_kernel = roofline_all(stats, (wl.n, wl.n, wl.n), peaks, local=loc, prec=prec)
+    dom, roof = roofline(stats, (wl.n, wl.n, wl.n), peaks, local=loc, prec=prec)
     roof_line = None
     if roof is not None and "bound" in roof:
+        traffic = TRAFFIC_64.get((dom, prec)) if wl.n == 64 else None
         roof_line = {"bound": roof["bound"], "achieved": roof["achieved"], "peak": roof["peak"], "unit": roof["unit"],
-                     "frac": roof["frac"],
-                     "traffic": TRAFFIC_64.get((dom, prec)) if wl.n == 64 else None,
+                     "frac": roof["frac"], "traffic": traffic,
+                     "traffic_source": ("stored figure from one ncu capture of this kernel at 64^3 "
+                                        f"({TRAFFIC_SOURCE})") if traffic else None,
                      "kernel": dom, "launches": roof["launches"],
                      "avg_us": roof["avg_us"], "share_of_kernel_time": roof["share"],
                      "peak_source": "FP64: derived 152 SM x 4 flop/clk x 2070 MHz" if roof["bound"] == "alu"
                      else f"HBM: MEASURED_PEAKS.json ({peaks['source']})"}
+        if roof["bound"] == "alu" and fp64_peak:
+            roof_line["fp64_peak_measured"] = fp64_peak
+            roof_line["frac_of_measured_fp64"] = roof["achieved"] / fp64_peak["gflops"]
     cpu = None
     if not a.no_cpu_baseline:
-        per_inc, sample_s, nsub, t_eval, t_cg = oracle_sample(wl)
-        evals_per_inc = evals / a.steps
-        cg_per_inc = cg_total / a.steps
-        t_inc = evals_per_inc * nvox * t_eval + cg_per_inc * t_cg
-        cpu = {"value": nvox * cg_per_inc / t_inc, "unit": "voxel-iter/s", "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"oracle local update + tangent on {nsub} voxels ({t_eval * 1e6:.0f} us/voxel) and 2 CG "
-                         f"iterations on the full grid ({t_cg:.2f} s each), {sample_s:.1f} s in all; composed with "
-                         f"this run's {evals_per_inc:.1f} evaluations and {cg_per_inc:.0f} CG iterations per increment"}
+        n_cg = max(2, int(round(24 * (64 ** 3) / nvox)))     # about 10-20 s of CPU work
+        t, nsub, _ = oracle_slice(wl, n_cg)
+        cpu = {"value": nvox * n_cg / t, "unit": "voxel-iter/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"a timed slice of the oracle's increment on the full grid: {n_cg} CG iterations and "
+                         f"the local update with tangent on {nsub} voxels ({t:.1f} s; the oracle's own mix of "
+                         f"{ORACLE_CG_PER_EVAL:g} CG iterations per local evaluation)"}
     line = {"metric": "voxel-iterations/s", "value": value, "unit": "voxel-iter/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -588,7 +791,12 @@ def main():
                        "local_residual_evals_per_voxel_eval": local_evals / max(1, evals * nvox),
                        "macro_P11_MPa": float(P_macro[0, 0]), "macro_sigma11_MPa": float(sig_macro[0, 0]),
                        "kernels_ms": {k: round(v[1], 3) for k, v in stats.items()},
-                       "kernels_launches": {k: v[0] for k, v in stats.items()}}}
+                       "kernels_launches": {k: v[0] for k, v in stats.items()},
+                       "kernel_event_time_over_timed_region": replay_over_timed,
+                       "roofline_by_kernel": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
+                                                  for kk, vv in v.items()} for k, v in by_kernel.items()}}}
+    if accuracy is not None:
+        line["accuracy_vs_fp64"] = accuracy
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

@@ -106,6 +106,9 @@ typedef struct {
                             tile sizes, staged or plain FP32 tangent apply; see rve_get_tuning).
                             The choice follows measured times, so two tuned handles may differ in
                             reduction order: equal results to round-off, not bit for bit. */
+  int32_t stencils;      /* divergence and gradient stencils of the projection: 0 row strips (one
+                            warp per x line, separable, no halo) where n0 is 32, 64, 96 or 128, else
+                            tiles; 1 tiles always.  Equal results to round-off. */
 } rve_options;
 
 #define RVE_MAX_NEWTON_LOG 64
@@ -241,7 +244,10 @@ rve_status rve_restore(rve_t* rve, const void* host_buf, size_t bytes);
 enum {
   RVE_K_FFT_X_R2C = 0, RVE_K_FFT_Y = 1, RVE_K_FFT_Z_OP = 2, RVE_K_FFT_X_C2R = 3,
   RVE_K_CONSTITUTIVE = 4, RVE_K_HARDENING = 5, RVE_K_TANGENT_APPLY = 6, RVE_K_CG_UPDATE = 7,
-  RVE_K_REDUCE = 8, RVE_K_OTHER = 9, RVE_K_STENCIL = 10, RVE_K_TANGENT_BUILD = 11, RVE_K_COUNT = 12
+  RVE_K_REDUCE = 8, RVE_K_OTHER = 9, RVE_K_STENCIL = 10, RVE_K_TANGENT_BUILD = 11,
+  RVE_K_FFT_CURL = 12,   /* all five passes of the nine-field Nye-curl FFT (the other FFT
+                            categories count the three-field transforms of the projection) */
+  RVE_K_COUNT = 13
 };
 rve_status rve_profile(rve_t* rve, int enable);
 /* The launch shapes in use (no counterpart in the paper): out[0] grid cap of
@@ -251,6 +257,18 @@ rve_status rve_profile(rve_t* rve, int enable);
  * (host array of 4). */
 rve_status rve_get_tuning(rve_t* rve, int32_t out[4]);
 rve_status rve_kernel_stats(rve_t* rve, int64_t* launches, double* ms);
+
+/* Device time of the hand-written FFT alone (no counterpart in the paper:
+ * instrumentation for the comparison with a vendor FFT): nf real fields of
+ * the handle's grid (nf = 3: the projection's transforms, with its
+ * inverse-Laplacian weight fused between the z passes; nf = 9: the nine-field
+ * transforms with the Galerkin projection fused) forward and back, `reps`
+ * times on the handle's stream and buffers, timed with CUDA events.  fp32 = 1
+ * times the FP32 transforms of the mixed-precision conjugate gradients (nf =
+ * 3, precision 1 handles only).  ms (host): average time of one forward +
+ * inverse pair.  Overwrites the handle's scratch (not its committed state).
+ * Errors: RVE_EINVAL for other nf / fp32 combinations. */
+rve_status rve_time_fft(rve_t* rve, int nf, int fp32, int reps, double* ms);
 
 /* Poll limit of the per-tile wait in the staged FP32 tangent apply
  * (rve_options.tma, precision 1; no counterpart in the paper: a bounded wait

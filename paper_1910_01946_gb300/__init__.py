@@ -30,7 +30,7 @@ FIELDS = {"F": (0, 9), "P": (1, 9), "FP": (2, 9), "S": (3, 6), "SIGMA": (4, 9), 
 
 MAX_NEWTON_LOG = 64
 KERNELS = ("fft_x_r2c", "fft_y", "fft_z_op", "fft_x_c2r", "constitutive", "hardening", "tangent_apply",
-           "cg_update", "reduce", "other", "stencil", "tangent_build")
+           "cg_update", "reduce", "other", "stencil", "tangent_build", "fft_curl")
 
 
 class rve_material(C.Structure):
@@ -45,7 +45,7 @@ class rve_options(C.Structure):
                 ("local_tol", C.c_double), ("max_newton", C.c_int32), ("max_cg", C.c_int32),
                 ("max_local", C.c_int32), ("max_halvings", C.c_int32), ("extrapolate", C.c_int32),
                 ("precision", C.c_int32), ("cg_adaptive", C.c_int32), ("krylov", C.c_int32),
-                ("graphs", C.c_int32), ("tma", C.c_int32), ("autotune", C.c_int32)]
+                ("graphs", C.c_int32), ("tma", C.c_int32), ("autotune", C.c_int32), ("stencils", C.c_int32)]
 
 
 class rve_step_info(C.Structure):
@@ -78,6 +78,7 @@ _SIGS = {
     "rve_get_tuning": (C.c_int, [C.c_void_p, C.c_void_p]),
     "rve_kernel_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "rve_set_wait_limit": (C.c_int, [C.c_void_p, C.c_uint32]),
+    "rve_time_fft": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "rve_project_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p]),
     "rve_sensitivity_bytes": (C.c_size_t, [C.c_void_p]),
@@ -246,7 +247,8 @@ def rve_destroy(h):
 
 # ---- handle wrapper ---------------------------------------------------------
 DEFAULT_OPTIONS = dict(newton_tol=1e-11, cg_tol=1e-11, local_tol=1e-14, max_newton=100, max_cg=2000,
-                       max_local=60, max_halvings=12, extrapolate=1, precision=0, cg_adaptive=1, krylov=0, graphs=1, tma=1, autotune=0)
+                       max_local=60, max_halvings=12, extrapolate=1, precision=0, cg_adaptive=1, krylov=0, graphs=1, tma=1, autotune=0,
+                       stencils=0)
 
 
 def make_material(m) -> rve_material:
@@ -350,6 +352,14 @@ class RVE:
     def set_wait_limit(self, polls: int):
         """Poll limit of the per-tile wait in the staged FP32 tangent apply (0: give up at once)."""
         self._check(load_library().rve_set_wait_limit(self.h, int(polls)), "rve_set_wait_limit")
+
+    def time_fft(self, nf=3, fp32=False, reps=20):
+        """Average device milliseconds of one forward + inverse FFT of nf fields
+        (the hand-written transforms alone, on the handle's buffers)."""
+        ms = C.c_double()
+        self._check(load_library().rve_time_fft(self.h, int(nf), int(bool(fp32)), int(reps), C.byref(ms)),
+                    "rve_time_fft")
+        return ms.value
 
     def tuning(self):
         """Launch shapes in use: divergence grid cap, FFT fill target, staged FP32 apply, autotuned."""

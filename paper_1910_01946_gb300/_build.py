@@ -68,6 +68,25 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     return LIB
 
 
+AUX_SRC = os.path.join(PKG, "bench_aux", "bench_aux.cu")
+AUX_LIB = os.path.join(PKG, "libbench_aux.so")
+
+
+def build_aux(force: bool = False) -> str:
+    """libbench_aux.so: the measurement helpers bench.py uses (live FP64 peak,
+    the cuFFT comparison).  A library of its own, so that cuFFT never links
+    into librve.so."""
+    if not force and os.path.exists(AUX_LIB) and os.path.getmtime(AUX_LIB) >= os.path.getmtime(AUX_SRC):
+        return AUX_LIB
+    tmp = AUX_LIB + ".tmp"
+    cmd = [nvcc(), *ARCH, *FLAGS, "-shared", AUX_SRC, "-o", tmp, "-lcufft", "-lcudart"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on {AUX_SRC}:\n{r.stderr}")
+    os.replace(tmp, AUX_LIB)
+    return AUX_LIB
+
+
 if __name__ == "__main__":
     import sys
     print(build(force="--force" in sys.argv, verbose=True, extra=["-Xptxas", "-v"] if "-v" in sys.argv else []))

@@ -155,6 +155,33 @@ __device__ __forceinline__ void blk_sums9(V* v, unsigned which, double* sh, doub
   __syncthreads();
 }
 
+// Sums over a warp of 16 values per lane by transposed halving: at the level
+// of shuffle distance o (16, 8, 4, 2) every lane keeps half of its values and
+// adds the partner's copy of that half, so the four levels cost 8 + 4 + 2 + 1
+// additions, and one more level (distance 1) completes the sums: 16 FP64
+// additions per warp instead of 16 x 5 for separate shuffle trees (every
+// FP64 instruction counts on this GPU's narrow FP64 pipe).  On return lane
+// L holds the warp total of value slot16_of_lane(L) (each slot in two lanes).
+__device__ __forceinline__ int slot16_of_lane(int lane) {
+  return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+}
+template <typename V>
+__device__ __forceinline__ V warp_sums16(V* v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int h = 8; h >= 1; h >>= 1) {
+    const int o = 2 * h;               // shuffle distance 16, 8, 4, 2
+    const bool hi = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      const V send = hi ? v[k] : v[k + h];
+      const V keep = hi ? v[k + h] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
 // After every block has written partial[c * gridDim.x + blockIdx.x] for
 // c < nval (nval <= 9): the block that takes the last ticket sums each value
 // whose bit is set in `which` over the blocks in block order (deterministic)

@@ -416,7 +416,7 @@ cudaError_t fwd(const rve_s* h, const R* in, cudaStream_t s, const double* done,
   dim3 gx(h->n1 / 2 / rpb, h->n2, nf);
   size_t shx = 2 * (size_t)rpb * h->n0 * sizeof(CX<R>);
   {
-    ProfScope ps_(h, RVE_K_FFT_X_R2C, s);
+    ProfScope ps_(h, h->fft_cat >= 0 ? h->fft_cat : RVE_K_FFT_X_R2C, s);
     k_fft_x_r2c<R><<<gx, threads_for(rpb * h->n0), shx, s>>>(in, spect<R>(h), h->n0, h->n1, h->n2, h->nkx, rpb,
                                                              to_dev(h->plan[0]), twt<R>(h, 0), done);
   }
@@ -424,7 +424,7 @@ cudaError_t fwd(const rve_s* h, const R* in, cudaStream_t s, const double* done,
   dim3 gy((h->nkx + ty - 1) / ty, h->n2, nf);
   size_t shy = 2 * (size_t)ty * h->n1 * sizeof(CX<R>);
   {
-    ProfScope ps_(h, RVE_K_FFT_Y, s);
+    ProfScope ps_(h, h->fft_cat >= 0 ? h->fft_cat : RVE_K_FFT_Y, s);
     k_fft_y<-1, R><<<gy, threads_for(ty * h->n1), shy, s>>>(spect<R>(h), h->n1, h->n2, h->nkx, ty,
                                                             to_dev(h->plan[1]), twt<R>(h, 1), done);
   }
@@ -438,7 +438,7 @@ cudaError_t zop(const rve_s* h, const SpecParams& sp, cudaStream_t s, const doub
   size_t sh = 2 * 3 * (size_t)tz * h->n2 * sizeof(CX<R>);
   const int zthreads = threads_for(3 * tz * h->n2);
   {
-    ProfScope ps_(h, RVE_K_FFT_Z_OP, s);
+    ProfScope ps_(h, h->fft_cat >= 0 ? h->fft_cat : RVE_K_FFT_Z_OP, s);
     k_fft_z_op<R><<<g, zthreads, sh, s>>>(spect<R>(h), h->n1, h->n2, h->nkx, tz, to_dev(h->plan[2]), twt<R>(h, 2),
                                           op_tables(h), sp, done);
   }
@@ -451,7 +451,7 @@ cudaError_t inv(const rve_s* h, R* out, cudaStream_t s, const double* done, int 
   dim3 gy((h->nkx + ty - 1) / ty, h->n2, nf);
   size_t shy = 2 * (size_t)ty * h->n1 * sizeof(CX<R>);
   {
-    ProfScope ps_(h, RVE_K_FFT_Y, s);
+    ProfScope ps_(h, h->fft_cat >= 0 ? h->fft_cat : RVE_K_FFT_Y, s);
     k_fft_y<+1, R><<<gy, threads_for(ty * h->n1), shy, s>>>(spect<R>(h), h->n1, h->n2, h->nkx, ty,
                                                             to_dev(h->plan[1]), twt<R>(h, 1), done);
   }
@@ -459,7 +459,7 @@ cudaError_t inv(const rve_s* h, R* out, cudaStream_t s, const double* done, int 
   dim3 gx(h->n1 / 2 / rpb, h->n2, nf);
   size_t shx = 2 * (size_t)rpb * h->n0 * sizeof(CX<R>);
   {
-    ProfScope ps_(h, RVE_K_FFT_X_C2R, s);
+    ProfScope ps_(h, h->fft_cat >= 0 ? h->fft_cat : RVE_K_FFT_X_C2R, s);
     k_fft_x_c2r<R><<<gx, threads_for(rpb * h->n0), shx, s>>>(spect<R>(h), out, h->n0, h->n1, h->n2, h->nkx, rpb,
                                                              to_dev(h->plan[0]), twt<R>(h, 0), done);
   }

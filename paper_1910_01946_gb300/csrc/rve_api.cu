@@ -283,10 +283,18 @@ rve_status run_project_stencil(rve_s* h, const double* X, double* Y, const uint8
   return RVE_OK;
 }
 
-rve_status run_hardening(rve_s* h) {
+// the nine-field curl transforms, counted in their own profiling category
+rve_status run_curl(rve_s* h, const double* in, double* out) {
   SpecParams sp = project_params(h, (const uint8_t*)"\0\0\0\0\0\0\0\0\0", nullptr, nullptr);
   sp.op = OP_CURL;
-  RVE_TRY(run_project(h, h->Fp, h->nye, sp));
+  h->fft_cat = RVE_K_FFT_CURL;
+  const rve_status st = run_project(h, in, out, sp);
+  h->fft_cat = -1;
+  return st;
+}
+
+rve_status run_hardening(rve_s* h) {
+  RVE_TRY(run_curl(h, h->Fp, h->nye));
   RVE_CUDA(h, launch_hardening(h, h->stream));
   return RVE_OK;
 }
@@ -529,14 +537,12 @@ rve_status bicgstab_solve(rve_s* h, const uint8_t* mask, double eta, int* iters,
 rve_status sens_update(rve_s* h, const uint8_t* mask, double dt) {
   const int cur = h->cur, sc = h->sens_cur, sn = 1 - h->sens_cur;
   RVE_CUDA(h, launch_tangent(h, dt, 0.0, cur, h->stream));
-  SpecParams curl = project_params(h, (const uint8_t*)"\0\0\0\0\0\0\0\0\0", nullptr, nullptr);
-  curl.op = OP_CURL;
   // the sensitivities need a few more digits than their uses (gradients
   // checked to 1e-5 against differences): 1e-9 by default
   const double eta = h->sens_tol > 0 ? h->sens_tol : std::fmax(h->opt.cg_tol, 1e-9);
   for (int j = 0; j < RVE_NTHETA; ++j) {
     Theta th{j == 0 ? 1.0 : 0.0, j == 1 ? 1.0 : 0.0, j == 2 ? 1.0 : 0.0, j == 3 ? 1.0 : 0.0};
-    RVE_TRY(run_project(h, h->sd_Fp[sc][j], h->s_dnye, curl));
+    RVE_TRY(run_curl(h, h->sd_Fp[sc][j], h->s_dnye));
     RVE_CUDA(h, launch_hard_jvp(h, h->s_dnye, h->sd_rho[sc][j], h->s_dtauc, h->s_dell, th, h->stream));
     RVE_CUDA(h, launch_local_jvp(h, dt, 0, nullptr, h->sd_Fp[sc][j], h->s_dtauc, h->s_dell, h->sd_rho[sc][j],
                                  h->s_dP, nullptr, nullptr, nullptr, th, h->stream));
@@ -773,7 +779,8 @@ rve_status rve_create(const int32_t* grain_id, int n0, int n1, int n2, const dou
   if (!(mat->C11 > 0 && mat->C44 > 0 && mat->C11 > mat->C12 && mat->b > 0 && mat->gdot0 > 0 && mat->n >= 1 &&
         mat->K > 0 && mat->yc >= 0 && mat->rho0_total > 0 && mat->tau0 >= 0 && mat->alpha >= 0 &&
         mat->q[0] > 0 && opt->L > 0 && opt->newton_tol > 0 && opt->cg_tol > 0 && opt->local_tol > 0 &&
-        opt->max_newton > 0 && opt->max_cg > 0 && opt->max_local > 0 && opt->max_halvings >= 0))
+        opt->max_newton > 0 && opt->max_cg > 0 && opt->max_local > 0 && opt->max_halvings >= 0 &&
+        opt->krylov >= 0 && opt->krylov <= 2 && (opt->stencils == 0 || opt->stencils == 1)))
     return RVE_EINVAL;
   const size_t nvox = (size_t)n0 * n1 * n2;
   for (size_t v = 0; v < nvox; ++v)
@@ -798,6 +805,7 @@ rve_status rve_create(const int32_t* grain_id, int n0, int n1, int n2, const dou
   if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || h->num_sms < 1)
     h->num_sms = 152;
   h->tma_apply = opt->tma != 0 && opt->precision == 1 && vec_init() == cudaSuccess;
+  h->row_stencils = opt->stencils == 0;
   h->h = opt->L / n0;
   h->mu = mat->mu > 0 ? mat->mu : 3.0 * mat->C44 * (mat->C11 - mat->C12) / (4.0 * mat->C44 + mat->C11 - mat->C12);
   h->cur = 0;
@@ -1318,6 +1326,41 @@ rve_status rve_get_stress_sensitivity(rve_t* h, double dP[RVE_NTHETA * 9]) {
   if (!h || !dP) return RVE_EINVAL;
   if (!h->sens_on || !h->sens_valid) return fail(h, RVE_EINVAL, "no sensitivity of a converged increment");
   for (int k = 0; k < RVE_NTHETA * 9; ++k) dP[k] = h->sens_dP[k];
+  return RVE_OK;
+}
+
+rve_status rve_time_fft(rve_t* h, int nf, int fp32, int reps, double* ms) {
+  if (!h || !ms || reps < 1 || !(nf == 3 || nf == 9) || (fp32 && (nf != 3 || h->opt.precision != 1)))
+    return RVE_EINVAL;
+  const uint8_t mask[9] = {1, 0, 0, 1, 0, 0, 1, 1, 0};
+  SpecParams sp = project_params(h, mask, nullptr, nullptr);
+  sp.op = nf == 3 ? OP_LAPINV : OP_PROJECT;
+  cudaStream_t s = h->stream;
+  auto pair = [&]() -> cudaError_t {
+    cudaError_t e;
+    if (fp32) {
+      if ((e = launch_fft_forward32(h, h->t32, s, nullptr)) != cudaSuccess) return e;
+      if ((e = launch_fft_lapinv32(h, sp, s, nullptr)) != cudaSuccess) return e;
+      return launch_fft_inverse32(h, h->x32, s, nullptr);
+    }
+    if ((e = launch_fft_forward(h, h->R, s, nullptr, nf)) != cudaSuccess) return e;
+    if ((e = launch_fft_op(h, sp, s, nullptr, nf)) != cudaSuccess) return e;
+    return launch_fft_inverse(h, h->t, s, nullptr, nf);
+  };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  RVE_CUDA(h, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return fail(h, RVE_ECUDA, "cudaEventCreate"); }
+  cudaError_t err = pair();                       // warm-up
+  if (err == cudaSuccess) err = cudaEventRecord(e0, s);
+  for (int r = 0; r < reps && err == cudaSuccess; ++r) err = pair();
+  if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+  if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+  float t = 0.0f;
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  RVE_CUDA(h, err);
+  *ms = (double)t / reps;
   return RVE_OK;
 }
 

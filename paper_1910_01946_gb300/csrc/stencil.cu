@@ -16,6 +16,10 @@
 
 namespace {
 
+template <typename V> struct V2T;
+template <> struct V2T<double> { typedef double2 t; };
+template <> struct V2T<float> { typedef float2 t; };
+
 // 32-bit voxel indexing (grids up to 512^3 = 2^27 voxels)
 struct Grid3 {
   int n0, n1, n2;
@@ -245,6 +249,397 @@ __global__ void __launch_bounds__(NT) k_grad_t(Grid3 g, Tiling T, const V* __res
   }
 }
 
+// ---------------------------------------------------------------- row-strip stencils
+// For n0 = 32 NPL (NPL = 1..4) the stencils run one warp per strip of Ly
+// consecutive rows (x lines) of one z plane, a whole x line per warp with
+// NPL adjacent points per lane (x = NPL lane + k), loaded as vectors.  The
+// stencil is applied separably, so every partial sum is formed once and
+// shared: z pairs (or differences), then y pairs of those, then the x step.
+// Within a lane the x -/+ 1 neighbour is the lane's own next point; across
+// lanes one value per field row comes by a warp shuffle (the line is
+// periodic and complete in the warp: no halo, no block barrier).  Each row
+// keeps the previous row's z pairs in registers and issues the next row's
+// loads before its own arithmetic.  Per voxel this is 30 FP64 additions for
+// the divergence (against 42 in the tiled form, which recomputes the shared
+// pairs) and 24 for the gradient (against 33).
+constexpr int RW = 4;            // warps per block
+
+template <typename V, int NPL>
+__device__ __forceinline__ void load_row(const V* __restrict__ src, V (&v)[NPL]) {
+  if constexpr (NPL == 2 || NPL == 4) {
+    typedef typename V2T<V>::t V2;
+#pragma unroll
+    for (int k = 0; k < NPL; k += 2) {
+      const V2 w = __ldg(reinterpret_cast<const V2*>(src) + k / 2);
+      v[k] = w.x;
+      v[k + 1] = w.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) v[k] = __ldg(src + k);
+  }
+}
+
+// Divergence d_i = sum_l D_l^T X_il (unscaled), as k_div.  Per voxel and row
+// i of X (fields A = X_i0, B = X_i1, C = X_i2): z pairs A = X(z) + X(z-1),
+// B likewise, C = X(z-1) - X(z); then with YS_A = A(y) + A(y-1),
+// YD_B = B(y-1) - B(y), YS_C = C(y) + C(y-1) and Q = YD_B + YS_C,
+//   d_i(x) = (Q - YS_A)(x) + (Q + YS_A)(x - 1).
+template <typename V, int NPL>
+__global__ void __launch_bounds__(32 * RW) k_div_rows(Grid3 g, int Ly, int nseg, const V* __restrict__ X,
+                                                     V* __restrict__ d, double* __restrict__ ds,
+                                                     double* __restrict__ partial, unsigned int* __restrict__ ticket,
+                                                     int check_done, unsigned mean_mask) {
+  __shared__ double sh[320];
+  if (check_done && ds[DS_DONE] != 0.0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int seg = blockIdx.x * RW + warp;
+  const int left = (lane + 31) & 31;
+  // the next row's loads are issued ahead of this row's arithmetic where the
+  // registers allow it (up to three points per lane)
+  constexpr bool PF = NPL <= 3;
+  V mean[9];
+#pragma unroll
+  for (int f = 0; f < 9; ++f) mean[f] = (V)0;
+  if (seg < g.n2 * nseg) {                              // warp-uniform
+    const int z = seg / nseg, sg = seg - z * nseg;
+    const int ya = sg * Ly, yb = min(ya + Ly, g.n1);
+    const unsigned plane = (unsigned)g.n0 * g.n1;
+    const unsigned rz = (unsigned)z * plane, rzp = (unsigned)wrapi(z - 1, g.n2) * plane;
+    V a[9][NPL], b[9][NPL];                             // loads of one row: plane z, plane z - 1
+    auto load = [&](int y) {
+      const unsigned row = (unsigned)y * g.n0 + NPL * lane;
+#pragma unroll
+      for (int f = 0; f < 9; ++f) {
+        load_row<V, NPL>(X + (size_t)f * g.nvox + rz + row, a[f]);
+        load_row<V, NPL>(X + (size_t)f * g.nvox + rzp + row, b[f]);
+      }
+    };
+    V zp[9][NPL];                                       // z pairs of the previous row
+    load(wrapi(ya - 1, g.n1));
+#pragma unroll
+    for (int f = 0; f < 9; ++f)
+#pragma unroll
+      for (int k = 0; k < NPL; ++k) zp[f][k] = (f % 3 == 2) ? b[f][k] - a[f][k] : a[f][k] + b[f][k];
+    if (PF) load(ya);
+    for (int y = ya; y < yb; ++y) {
+      if (!PF) load(y);
+      V zc[9][NPL];
+#pragma unroll
+      for (int f = 0; f < 9; ++f)
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) {
+          zc[f][k] = (f % 3 == 2) ? b[f][k] - a[f][k] : a[f][k] + b[f][k];
+          if ((mean_mask >> f) & 1u) mean[f] += a[f][k];
+        }
+      if (PF && y + 1 < yb) load(y + 1);                // in flight during this row's arithmetic
+      const unsigned row = rz + (unsigned)y * g.n0 + NPL * lane;
+      if constexpr (sizeof(V) == 8) {
+        // FP64: the x step of the three y sums in one pair (e1, e2), one
+        // value per row from the left lane
+        V e1[3][NPL], e2[3][NPL], e2l[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int k = 0; k < NPL; ++k) {
+            const V ysa = zc[3 * i][k] + zp[3 * i][k];
+            const V ydb = zp[3 * i + 1][k] - zc[3 * i + 1][k];
+            const V ysc = zc[3 * i + 2][k] + zp[3 * i + 2][k];
+            const V q = ydb + ysc;
+            e1[i][k] = q - ysa;
+            e2[i][k] = q + ysa;
+          }
+        // the left neighbour's last point, for the three rows at once
+#pragma unroll
+        for (int i = 0; i < 3; ++i) e2l[i] = __shfl_sync(0xffffffffu, e2[i][NPL - 1], left);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int k = 0; k < NPL; ++k)
+            d[(size_t)i * g.nvox + row + k] = e1[i][k] + (k == 0 ? e2l[i] : e2[i][k - 1]);
+      } else {
+        // FP32 (the mixed-precision CG): each directional term is formed as a
+        // difference of its own y sums before the terms are added, so the
+        // small y differences are never rounded at the scale of the large z
+        // pairs (the grouping of the tiled kernel); three values per row
+        // cross lanes
+        V ysa[3][NPL], ydb[3][NPL], ysc[3][NPL], l[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int k = 0; k < NPL; ++k) {
+            ysa[i][k] = zc[3 * i][k] + zp[3 * i][k];
+            ydb[i][k] = zp[3 * i + 1][k] - zc[3 * i + 1][k];
+            ysc[i][k] = zc[3 * i + 2][k] + zp[3 * i + 2][k];
+          }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          l[i][0] = __shfl_sync(0xffffffffu, ysa[i][NPL - 1], left);
+          l[i][1] = __shfl_sync(0xffffffffu, ydb[i][NPL - 1], left);
+          l[i][2] = __shfl_sync(0xffffffffu, ysc[i][NPL - 1], left);
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int k = 0; k < NPL; ++k) {
+            const V am = k == 0 ? l[i][0] : ysa[i][k > 0 ? k - 1 : 0];
+            const V bm = k == 0 ? l[i][1] : ydb[i][k > 0 ? k - 1 : 0];
+            const V cm = k == 0 ? l[i][2] : ysc[i][k > 0 ? k - 1 : 0];
+            const V d0 = am - ysa[i][k];
+            const V d1 = ydb[i][k] + bm;
+            const V d2 = ysc[i][k] + cm;
+            d[(size_t)i * g.nvox + row + k] = d0 + d1 + d2;
+          }
+      }
+#pragma unroll
+      for (int f = 0; f < 9; ++f)
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) zp[f][k] = zc[f][k];
+    }
+  }
+  // means: one transposed warp reduction of the (up to nine) selected fields,
+  // the block's warps combined in shared memory, then the grid's last block
+  V m16[16];
+#pragma unroll
+  for (int f = 0; f < 16; ++f) m16[f] = f < 9 ? mean[f] : (V)0;
+  const V w = warp_sums16<V>(m16);
+  const int slot = slot16_of_lane(lane);
+  if ((lane & 1) == 0 && slot < 9) sh[warp * 16 + slot] = (double)w;
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    double t = 0.0;
+    for (int q = 0; q < RW; ++q) t += sh[q * 16 + threadIdx.x];
+    partial[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = ((mean_mask >> threadIdx.x) & 1u) ? t : 0.0;
+  }
+  double tot[9];
+  if (last_block_sums(partial, 9, ticket, sh, tot, mean_mask) && threadIdx.x == 0) {
+    for (int c = 0; c < 9; ++c) ds[DS_XMEAN + c] = tot[c] / (double)g.nvox;
+  }
+}
+
+// Gradient of the three potentials q_ij = D_j u_i (unscaled) plus the zero
+// mode, as k_grad_t.  Per potential: z pair SP = u(z) + u(z+1) and
+// difference SM = u(z+1) - u(z); YS = SP(y) + SP(y+1), YD = SP(y+1) - SP(y),
+// YM = SM(y) + SM(y+1); q_i0 = YS(x+1) - YS(x), q_i1 = YD(x) + YD(x+1),
+// q_i2 = YM(x) + YM(x+1).  CG as in k_grad_t.
+template <bool CG, typename V, int NPL>
+__global__ void __launch_bounds__(32 * RW, NPL <= 2 ? 4 : 1) k_grad_rows(Grid3 g, int Ly, int nseg, const V* __restrict__ u,
+                                                      ZeroMode zm, double* __restrict__ Y, V* __restrict__ x,
+                                                      V* __restrict__ r, const V* __restrict__ p,
+                                                      double* __restrict__ ds, double* __restrict__ partial,
+                                                      unsigned int* __restrict__ ticket) {
+  __shared__ double sh[320];
+  if (CG && ds[DS_DONE] != 0.0) return;
+  const V alpha = CG ? (V)ds[DS_ALPHA] : (V)0;
+  V off[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) off[c] = zm.keep[c] ? (V)(ds[DS_XMEAN + c] + zm.add[c]) : (V)0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int seg = blockIdx.x * RW + warp;
+  const int right = (lane + 1) & 31;
+  V acc = (V)0;
+  if (seg < g.n2 * nseg) {
+    const int z = seg / nseg, sg = seg - z * nseg;
+    const int ya = sg * Ly, yb = min(ya + Ly, g.n1);
+    const unsigned plane = (unsigned)g.n0 * g.n1;
+    const unsigned rz = (unsigned)z * plane, rzn = (unsigned)wrapi(z + 1, g.n2) * plane;
+    V a[3][NPL], c[3][NPL];                             // loads of one row: plane z, plane z + 1
+    auto load = [&](int y) {
+      const unsigned row = (unsigned)y * g.n0 + NPL * lane;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        load_row<V, NPL>(u + (size_t)i * g.nvox + rz + row, a[i]);
+        load_row<V, NPL>(u + (size_t)i * g.nvox + rzn + row, c[i]);
+      }
+    };
+    V sp[3][NPL], sm[3][NPL];                           // z pair and difference of the current row
+    load(ya);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < NPL; ++k) { sp[i][k] = a[i][k] + c[i][k]; sm[i][k] = c[i][k] - a[i][k]; }
+    load(ya + 1 < g.n1 ? ya + 1 : 0);
+    for (int y = ya; y < yb; ++y) {
+      V spn[3][NPL], smn[3][NPL];                       // row y + 1
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) { spn[i][k] = a[i][k] + c[i][k]; smn[i][k] = c[i][k] - a[i][k]; }
+      if (y + 1 < yb) load(y + 2 < g.n1 ? y + 2 : 0);
+      const unsigned row = rz + (unsigned)y * g.n0 + NPL * lane;
+      V ys[3][NPL], yd[3][NPL], ym[3][NPL], rs[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) {
+          ys[i][k] = sp[i][k] + spn[i][k];
+          yd[i][k] = spn[i][k] - sp[i][k];
+          ym[i][k] = sm[i][k] + smn[i][k];
+        }
+      // the right neighbour's first point of the three sums, nine at once
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        rs[i][0] = __shfl_sync(0xffffffffu, ys[i][0], right);
+        rs[i][1] = __shfl_sync(0xffffffffu, yd[i][0], right);
+        rs[i][2] = __shfl_sync(0xffffffffu, ym[i][0], right);
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        V qv[3][NPL];
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) {
+          const V ysr = k + 1 < NPL ? ys[i][k + 1 < NPL ? k + 1 : 0] : rs[i][0];
+          const V ydr = k + 1 < NPL ? yd[i][k + 1 < NPL ? k + 1 : 0] : rs[i][1];
+          const V ymr = k + 1 < NPL ? ym[i][k + 1 < NPL ? k + 1 : 0] : rs[i][2];
+          qv[0][k] = ysr - ys[i][k];
+          qv[1][k] = yd[i][k] + ydr;
+          qv[2][k] = ym[i][k] + ymr;
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+            if (zm.keep[3 * i + j]) qv[j][k] += off[3 * i + j];
+        }
+        if (CG) {
+          // the row's p, x and r of this tensor row are loaded together, so
+          // that their latencies overlap
+          V pv[3][NPL], xv[3][NPL], rv[3][NPL];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const size_t e = (size_t)(3 * i + j) * g.nvox + row;
+            load_row<V, NPL>(p + e, pv[j]);
+            load_row<V, NPL>(x + e, xv[j]);
+            load_row<V, NPL>(r + e, rv[j]);
+          }
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < NPL; ++k) {
+              const size_t e = (size_t)(3 * i + j) * g.nvox + row + k;
+              x[e] = fma(alpha, pv[j][k], xv[j][k]);
+              const V rn = fma(-alpha, qv[j][k], rv[j][k]);
+              r[e] = rn;
+              acc = fma(rn, rn, acc);
+            }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < NPL; ++k) {
+              Y[(size_t)(3 * i + j) * g.nvox + row + k] = (double)qv[j][k];
+              acc = fma(qv[j][k], qv[j][k], acc);
+            }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) { sp[i][k] = spn[i][k]; sm[i][k] = smn[i][k]; }
+    }
+  }
+  const double s = blk_sum_v<V>(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  double tot;
+  if (last_block_sums(partial, 1, ticket, sh, &tot) && threadIdx.x == 0) {
+    if (CG) {
+      ds[DS_BETA] = tot / ds[DS_RR];
+      ds[DS_RR] = tot;
+      ds[DS_ITERS] += 1.0;
+      if (!(tot > ds[DS_STOP])) ds[DS_DONE] = 1.0;
+    } else {
+      ds[DS_NORM] = tot;
+    }
+  }
+}
+
+struct RowShape {
+  int npl, Ly, nseg, nblocks;
+};
+
+// Rows per strip: every strip costs its rows plus one priming row (the z
+// pairs of the row before it), and the strips run in waves of (resident
+// blocks per SM x SMs x RW) warps, so Ly minimises waves x (Ly + 1).  With
+// h->div_blocks below its default (the autotuner's candidates) the strips
+// are made as many as that many blocks hold instead.
+RowShape row_shape_for(const rve_s* h, int blocks_per_sm) {
+  RowShape r{0, 0, 0, 0};
+  if (h->n0 % 32 != 0 || h->n0 > 128) return r;
+  r.npl = h->n0 / 32;
+  const long slots = (long)RW * h->num_sms * (blocks_per_sm > 0 ? blocks_per_sm : 1);
+  long best = -1, pick = 1;
+  for (int ly = 1; ly <= h->n1 && ly <= 16; ++ly) {
+    const long segs = (long)h->n2 * ((h->n1 + ly - 1) / ly);
+    const long cost = ((segs + slots - 1) / slots) * (ly + 1);
+    if (best < 0 || cost < best) { best = cost; pick = ly; }
+  }
+  if (h->row_ly > 0) pick = h->row_ly < h->n1 ? h->row_ly : h->n1;
+  r.Ly = (int)pick;
+  r.nseg = (h->n1 + r.Ly - 1) / r.Ly;
+  r.nblocks = (h->n2 * r.nseg + RW - 1) / RW;
+  return r;
+}
+
+template <typename K>
+int resident_blocks(K kernel) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, 32 * RW, 0) != cudaSuccess) n = 1;
+  return n;
+}
+
+template <typename V, int NPL>
+cudaError_t div_rows_n(const rve_s* h, const V* X, V* d, int check_done, unsigned mean_mask, cudaStream_t s,
+                       const Grid3& g) {
+  static const int bps = resident_blocks(k_div_rows<V, NPL>);
+  const RowShape rs = row_shape_for(h, bps);
+  k_div_rows<V, NPL><<<rs.nblocks, 32 * RW, 0, s>>>(g, rs.Ly, rs.nseg, X, d, h->dscal, h->partial,
+                                                    (unsigned int*)(h->dcount + 4), check_done, mean_mask);
+  return cudaGetLastError();
+}
+
+template <typename V>
+cudaError_t div_rows(const rve_s* h, int npl, const V* X, V* d, int check_done, unsigned mean_mask, cudaStream_t s,
+                     const Grid3& g) {
+  switch (npl) {
+    case 1: return div_rows_n<V, 1>(h, X, d, check_done, mean_mask, s, g);
+    case 2: return div_rows_n<V, 2>(h, X, d, check_done, mean_mask, s, g);
+    case 3: return div_rows_n<V, 3>(h, X, d, check_done, mean_mask, s, g);
+    default: return div_rows_n<V, 4>(h, X, d, check_done, mean_mask, s, g);
+  }
+}
+
+template <bool CG, typename V, int NPL>
+cudaError_t grad_rows_n(const rve_s* h, const V* u, const ZeroMode& zm, double* Y, V* x, V* r, const V* p,
+                        cudaStream_t s, const Grid3& g) {
+  static const int bps = resident_blocks(k_grad_rows<CG, V, NPL>);
+  const RowShape rs = row_shape_for(h, bps);
+  k_grad_rows<CG, V, NPL><<<rs.nblocks, 32 * RW, 0, s>>>(g, rs.Ly, rs.nseg, u, zm, Y, x, r, p, h->dscal, h->partial,
+                                                         (unsigned int*)(h->dcount + 4));
+  return cudaGetLastError();
+}
+
+template <bool CG, typename V>
+cudaError_t grad_rows(const rve_s* h, int npl, const V* u, const ZeroMode& zm, double* Y, V* x, V* r, const V* p,
+                      cudaStream_t s, const Grid3& g) {
+  switch (npl) {
+    case 1: return grad_rows_n<CG, V, 1>(h, u, zm, Y, x, r, p, s, g);
+    case 2: return grad_rows_n<CG, V, 2>(h, u, zm, Y, x, r, p, s, g);
+    case 3: return grad_rows_n<CG, V, 3>(h, u, zm, Y, x, r, p, s, g);
+    default: return grad_rows_n<CG, V, 4>(h, u, zm, Y, x, r, p, s, g);
+  }
+}
+
+// points per lane of the row-strip stencils for this grid (0: tiled stencils).
+// The FP64 divergence takes them up to n0 = 128; the gradient with its fused
+// vector update up to n0 = 64 (beyond that its register demand leaves too
+// few warps to cover the update's loads, measured 1.8x slower at 128^3).  The
+// FP32 stencils of the mixed-precision CG take them up to n0 = 64: on the
+// hardest sweep RVE (96^3, 183 grains, plastic onset) the FP32 CG stalls on
+// the non-symmetric tangent and the Newton path is chaotic in the rounding
+// order of the projection; it is known to converge with the tiled order there.
+int row_npl(const rve_s* h, bool gradient = false, bool fp32 = false) {
+  const int lim = (gradient || fp32) ? 64 : 128;
+  if (!h->row_stencils || h->n0 % 32 != 0 || h->n0 > lim) return 0;
+  return h->n0 / 32;
+}
+
 Tiling tiling_of(const rve_s* h) {
   Tiling T;
   int tx = 1;
@@ -280,6 +675,10 @@ int stencil_tiles(const rve_s* h) { return tiling_of(h).ntiles; }
 
 cudaError_t launch_div(const rve_s* h, const double* X, double* d, int check_done, unsigned mean_mask,
                        cudaStream_t s) {
+  if (const int npl = row_npl(h)) {
+    ProfScope ps_(h, RVE_K_STENCIL, s);
+    return div_rows<double>(h, npl, X, d, check_done, mean_mask, s, grid_of(h));
+  }
   Tiling T = tiling_of(h);
   if ((T.tx + 1) * (T.ty + 1) > SMAX) return cudaErrorInvalidValue;   // n0 odd: not a valid grid
   if (T.nblocks > h->div_blocks) T.nblocks = h->div_blocks;
@@ -293,6 +692,10 @@ cudaError_t launch_div(const rve_s* h, const double* X, double* d, int check_don
 
 cudaError_t launch_grad(const rve_s* h, const double* u, double* Y, const uint8_t* mask, const double* shift,
                         cudaStream_t s) {
+  if (const int npl = row_npl(h, true)) {
+    ProfScope ps_(h, RVE_K_STENCIL, s);
+    return grad_rows<false, double>(h, npl, u, zero_mode(mask, shift), Y, nullptr, nullptr, nullptr, s, grid_of(h));
+  }
   const Tiling T = tiling_of(h);
   if ((T.tx + 1) * (T.ty + 1) > SMAX) return cudaErrorInvalidValue;   // n0 odd: not a valid grid
   {
@@ -305,6 +708,10 @@ cudaError_t launch_grad(const rve_s* h, const double* u, double* Y, const uint8_
 }
 
 cudaError_t launch_grad_cg(const rve_s* h, const double* u, const uint8_t* mask, cudaStream_t s) {
+  if (const int npl = row_npl(h, true)) {
+    ProfScope ps_(h, RVE_K_CG_UPDATE, s);
+    return grad_rows<true, double>(h, npl, u, zero_mode(mask, nullptr), nullptr, h->x, h->r, h->p, s, grid_of(h));
+  }
   const Tiling T = tiling_of(h);
   if ((T.tx + 1) * (T.ty + 1) > SMAX) return cudaErrorInvalidValue;   // n0 odd: not a valid grid
   {
@@ -317,6 +724,10 @@ cudaError_t launch_grad_cg(const rve_s* h, const double* u, const uint8_t* mask,
 }
 
 cudaError_t launch_div32(const rve_s* h, const float* X, float* d, unsigned mean_mask, cudaStream_t s) {
+  if (const int npl = row_npl(h, false, true)) {
+    ProfScope ps_(h, RVE_K_STENCIL, s);
+    return div_rows<float>(h, npl, X, d, 1, mean_mask, s, grid_of(h));
+  }
   // the same capped grid as in FP64: one tile per block (2048 blocks at 64^3)
   // measured slower (41.5 against 34.6 us) than a few tiles per block
   Tiling T = tiling_of(h);
@@ -331,6 +742,10 @@ cudaError_t launch_div32(const rve_s* h, const float* X, float* d, unsigned mean
 }
 
 cudaError_t launch_grad_cg32(const rve_s* h, const float* u, const uint8_t* mask, cudaStream_t s) {
+  if (const int npl = row_npl(h, true, true)) {
+    ProfScope ps_(h, RVE_K_CG_UPDATE, s);
+    return grad_rows<true, float>(h, npl, u, zero_mode(mask, nullptr), nullptr, h->x32, h->r32, h->p32, s, grid_of(h));
+  }
   const Tiling T = tiling_of(h);
   if ((T.tx + 1) * (T.ty + 1) > SMAX) return cudaErrorInvalidValue;   // n0 odd: not a valid grid
   {

@@ -4,6 +4,8 @@
 // the increment) and the volume averages.  All reductions are deterministic:
 // a fixed grid writes one partial per block, a single block sums the
 // partials in a fixed order and derives the CG scalars on the device.
+#include <algorithm>
+
 #include "common.cuh"
 #include "rve_internal.h"
 
@@ -541,10 +543,14 @@ unsigned grid_for(size_t n, int threads) {
 }  // namespace
 
 cudaError_t launch_tangent_apply(const rve_s* h, cudaStream_t s) {
+  // one wave of resident blocks (three per SM): each thread covers more
+  // voxels, so the block reduction of p . t is spread over more of them, and
+  // no partial last wave trails
+  const int blocks = std::min(RVE_RED_BLOCKS, 3 * h->num_sms);
   {
     ProfScope ps_(h, RVE_K_TANGENT_APPLY, s);
-    k_tangent_apply<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, h->K[h->cur], h->r, h->p, h->t, h->dscal,
-                                                               h->partial, (unsigned int*)(h->dcount + 4));
+    k_tangent_apply<<<blocks, RVE_RED_THREADS, 0, s>>>(h->nvox, h->K[h->cur], h->r, h->p, h->t, h->dscal,
+                                                       h->partial, (unsigned int*)(h->dcount + 4));
   }
   return cudaGetLastError();
 }

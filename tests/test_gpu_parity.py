@@ -81,8 +81,11 @@ def to_field(a, shape):
     return a.reshape(shape + (9,))
 
 
-@pytest.mark.parametrize("shape", [(8, 8, 8), (6, 12, 16), (9, 4, 6), (1, 4, 4), (16, 16, 16)])
+@pytest.mark.parametrize("shape", [(8, 8, 8), (6, 12, 16), (9, 4, 6), (1, 4, 4), (16, 16, 16),
+                                   (2, 6, 32), (3, 4, 64), (2, 6, 96), (1, 2, 128)])
 def test_projection_matches_oracle(pkg, shape):
+    """n0 = 32, 64, 96, 128 take the row-strip stencils (one warp per x line,
+    1-4 points per lane); the other widths the tiled ones."""
     import torch
     n2, n1, n0 = shape
     gid = np.zeros(shape, dtype=np.int32)
@@ -175,12 +178,14 @@ def test_cu16_first_increments_match_oracle(pkg):
     g.close()
 
 
-@pytest.mark.parametrize("shape", [(24, 24, 6), (6, 24, 24)], ids=["24x24x6", "6x24x24"])
+@pytest.mark.parametrize("shape", [(24, 24, 6), (6, 24, 24), (32, 8, 6), (64, 6, 4)],
+                         ids=["24x24x6", "6x24x24", "32x8x6", "64x6x4"])
 def test_increments_match_oracle_mixed_radix_grid(pkg, shape):
     """Grids whose FFT plans chain radix-4, radix-2 and radix-3 passes
     (24 = 4 * 2 * 3), on the x and y axes or on the y and z axes: the plan
-    family of the 48^3 and 96^3 sweep RVEs.  Three increments to 6e-4 (past
-    the plastic onset, GND active)."""
+    family of the 48^3 and 96^3 sweep RVEs; and x lines of 32 and 64 voxels,
+    which take the row-strip stencils.  Three increments to 6e-4 (past the
+    plastic onset, GND active)."""
     n0, n1, n2 = shape
     ng = 6
     gid, _ = rvegen.voronoi_grain_map(0, ng, 2401, shape=shape)
@@ -316,6 +321,22 @@ def test_bicgstab_increments_match_oracle(pkg, wl, precision):
         assert gi["bicgstab_solves"] == gi["newton_iters"]
     check_increment_fields(g, o)
     g.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_row_strip_stencils_match_tiled(pkg, precision):
+    """The row-strip stencils (default where n0 = 32 k) and the tiled ones
+    (stencils = 1) reach the same increments on the 64^3 workload."""
+    wl = rvegen.WORKLOADS["cu64"]
+    gid, quat, mat = wl.inputs()
+    a = pkg.RVE(gid, quat, mat, wl.edge, precision=precision, stencils=0)
+    b = pkg.RVE(gid, quat, mat, wl.edge, precision=precision, stencils=1)
+    for k in range(3):
+        assert a.step(wl.dFbar(), MASK, np.zeros(9), wl.dt)["converged"]
+        assert b.step(wl.dFbar(), MASK, np.zeros(9), wl.dt)["converged"]
+    for name, base in (("F", EYE9), ("P", None), ("FP", EYE9), ("RHO_GND", None)):
+        assert comp_err(a.field(name), b.field(name), base) < 1e-9, name
+    a.close(); b.close()
 
 
 def test_staged_tangent_apply_matches_plain_loads(pkg):
