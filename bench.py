@@ -164,6 +164,7 @@ def kernel_models(n0, n1, n2, local=None):
     return {
         "fft_x_r2c": f3["x"],
         "fft_y": f3["y"],
+        "fft_y_inv": f3["y"],
         "fft_z_op": f3["z"],
         "fft_x_c2r": f3["x"],
         "fft_curl": (curl[0], curl[1]),
@@ -183,7 +184,7 @@ def kernel_models(n0, n1, n2, local=None):
 
 # the FP32 conjugate-gradient kernels of the mixed path: half the bytes of the
 # FP64 model, and their FP32 arithmetic is far below the FP32 peak, so HBM binds
-FP32_CG = ("tangent_apply", "stencil", "cg_update", "fft_x_r2c", "fft_y", "fft_z_op", "fft_x_c2r")
+FP32_CG = ("tangent_apply", "stencil", "cg_update", "fft_x_r2c", "fft_y", "fft_y_inv", "fft_z_op", "fft_x_c2r")
 
 
 

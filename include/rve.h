@@ -247,7 +247,8 @@ enum {
   RVE_K_REDUCE = 8, RVE_K_OTHER = 9, RVE_K_STENCIL = 10, RVE_K_TANGENT_BUILD = 11,
   RVE_K_FFT_CURL = 12,   /* all five passes of the nine-field Nye-curl FFT (the other FFT
                             categories count the three-field transforms of the projection) */
-  RVE_K_COUNT = 13
+  RVE_K_FFT_Y_INV = 13,  /* the inverse y pass (RVE_K_FFT_Y counts the forward one) */
+  RVE_K_COUNT = 14
 };
 rve_status rve_profile(rve_t* rve, int enable);
 /* The launch shapes in use (no counterpart in the paper): out[0] grid cap of

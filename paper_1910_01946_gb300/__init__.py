@@ -30,7 +30,7 @@ FIELDS = {"F": (0, 9), "P": (1, 9), "FP": (2, 9), "S": (3, 6), "SIGMA": (4, 9), 
 
 MAX_NEWTON_LOG = 64
 KERNELS = ("fft_x_r2c", "fft_y", "fft_z_op", "fft_x_c2r", "constitutive", "hardening", "tangent_apply",
-           "cg_update", "reduce", "other", "stencil", "tangent_build", "fft_curl")
+           "cg_update", "reduce", "other", "stencil", "tangent_build", "fft_curl", "fft_y_inv")
 
 
 class rve_material(C.Structure):

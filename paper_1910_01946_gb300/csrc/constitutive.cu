@@ -22,6 +22,8 @@
 // residual r(S) = S - C : (Fe^T Fe - I)/2, Fe = F Fp^-1, solved from a warm
 // start with the exact Jacobian and step halving (a step is taken only if it
 // lowers max|r| and keeps every |dgam| <= dgam_max).
+#include <algorithm>
+
 #include "common.cuh"
 #include "rve_internal.h"
 
@@ -321,85 +323,118 @@ __device__ __forceinline__ void piola(const VoxelIn& in, const double* S, const 
   mat3_mul(in.R, U, P);
 }
 
-// Local Newton on S (data-dependent iteration counts): writes S, dgam and P.
+// Local Newton on S at one voxel (data-dependent iteration counts): writes S,
+// dgam and P; returns the Newton iterations, residual evaluations and whether
+// it failed.
+__device__ __forceinline__ void local_voxel(size_t nvox, size_t v, const int32_t* __restrict__ grain,
+                                            const double* __restrict__ grainR, const double* __restrict__ Fin,
+                                            const double* __restrict__ xdir, double lambda,
+                                            const double* __restrict__ Fp0inv, const double* __restrict__ tauc_g,
+                                            const double* __restrict__ Swarm, double* __restrict__ Sout,
+                                            double* __restrict__ dgout, double* __restrict__ Pout, double dt,
+                                            const Consts& c, int& iters, int& evals, int& failed) {
+  VoxelIn in;
+  load_voxel(nvox, v, grain, grainR, Fin, xdir, lambda, Fp0inv, tauc_g, in);
+  const double* A = in.A;
+  const double* tinv = in.tinv;      // 1 / tauc
+  double S[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) S[k] = Swarm[k * nvox + v];
+
+  Eval e;
+  evaluate(c, S, A, tinv, dt, e);
+  ++evals;
+  if (!(e.rn < INFINITY)) {             // warm start rejected: restart from the elastic-free state
+#pragma unroll
+    for (int k = 0; k < 6; ++k) S[k] = 0.0;
+    evaluate(c, S, A, tinv, dt, e);
+    ++evals;
+  }
+  double J[36], dgp[12];
+  int piv[6];
+  bool conv = e.rn <= c.local_tol_abs;
+  while (!conv && iters < c.max_local) {
+    jacobian(c, e, tinv, dt, J, dgp);
+    lu6(J, piv);
+    double d[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) d[k] = -e.r[k];
+    lu6_solve(J, piv, d);
+    double lam = 1.0;
+    bool acc = false;
+    for (int hv = 0; hv <= c.max_halvings; ++hv) {
+      double St[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) St[k] = fma(lam, d[k], S[k]);
+      Eval et;
+      evaluate(c, St, A, tinv, dt, et);
+      ++evals;
+      if (et.rn < e.rn) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) S[k] = St[k];
+        e = et;
+        acc = true;
+        break;
+      }
+      lam *= 0.5;
+    }
+    ++iters;
+    if (!acc) {                          // no decrease: round-off floor or failure
+      conv = e.rn <= c.floor_abs;
+      break;
+    }
+    conv = e.rn <= c.local_tol_abs;
+  }
+  failed = conv ? 0 : 1;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) Sout[k * nvox + v] = S[k];
+#pragma unroll
+  for (int a = 0; a < 12; ++a) dgout[a * nvox + v] = e.dg[a];
+  double P[9];
+  piola(in, S, e.Minv, P);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Pout[k * nvox + v] = P[k];
+}
+
+// Local update over all voxels.  The number of local Newton iterations
+// differs from voxel to voxel (grains near their yield point need several),
+// so the kernel is persistent and balanced dynamically: each warp takes the
+// next chunk of 32 voxels from a device counter (counters[6], zeroed before
+// the launch) until none is left, and an SM whose voxels converge quickly
+// takes more chunks.  Each voxel's arithmetic is the same as with a fixed
+// assignment.
 __global__ void __launch_bounds__(128) k_local(
     size_t nvox, const int32_t* __restrict__ grain, const double* __restrict__ grainR,
     const double* __restrict__ Fin, const double* __restrict__ xdir, double lambda,
     const double* __restrict__ Fp0inv, const double* __restrict__ tauc_g, const double* __restrict__ Swarm,
     double* __restrict__ Sout, double* __restrict__ dgout, double* __restrict__ Pout,
     int32_t* __restrict__ counters, double dt, Consts c) {
-  const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int iters = 0, failed = 0, evals = 0;
-  if (v < nvox) {
-    VoxelIn in;
-    load_voxel(nvox, v, grain, grainR, Fin, xdir, lambda, Fp0inv, tauc_g, in);
-    const double* A = in.A;
-    const double* tinv = in.tinv;      // 1 / tauc
-    double S[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) S[k] = Swarm[k * nvox + v];
-
-    Eval e;
-    evaluate(c, S, A, tinv, dt, e);
-    ++evals;
-    if (!(e.rn < INFINITY)) {             // warm start rejected: restart from the elastic-free state
-#pragma unroll
-      for (int k = 0; k < 6; ++k) S[k] = 0.0;
-      evaluate(c, S, A, tinv, dt, e);
-      ++evals;
-    }
-    double J[36], dgp[12];
-    int piv[6];
-    bool conv = e.rn <= c.local_tol_abs;
-    while (!conv && iters < c.max_local) {
-      jacobian(c, e, tinv, dt, J, dgp);
-      lu6(J, piv);
-      double d[6];
-#pragma unroll
-      for (int k = 0; k < 6; ++k) d[k] = -e.r[k];
-      lu6_solve(J, piv, d);
-      double lam = 1.0;
-      bool acc = false;
-      for (int hv = 0; hv <= c.max_halvings; ++hv) {
-        double St[6];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) St[k] = fma(lam, d[k], S[k]);
-        Eval et;
-        evaluate(c, St, A, tinv, dt, et);
-        ++evals;
-        if (et.rn < e.rn) {
-#pragma unroll
-          for (int k = 0; k < 6; ++k) S[k] = St[k];
-          e = et;
-          acc = true;
-          break;
-        }
-        lam *= 0.5;
-      }
-      ++iters;
-      if (!acc) {                          // no decrease: round-off floor or failure
-        conv = e.rn <= c.floor_abs;
-        break;
-      }
-      conv = e.rn <= c.local_tol_abs;
-    }
-    failed = conv ? 0 : 1;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) Sout[k * nvox + v] = S[k];
-#pragma unroll
-    for (int a = 0; a < 12; ++a) dgout[a * nvox + v] = e.dg[a];
-    double P[9];
-    piola(in, S, e.Minv, P);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) Pout[k * nvox + v] = P[k];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const long nchunks = (long)((nvox + 31) / 32);
+  int mx = 0, nf = 0;
+  unsigned si = 0, se = 0;
+  for (;;) {
+    int chunk = 0;
+    if (lane == 0) chunk = atomicAdd(&counters[6], 1);
+    chunk = __shfl_sync(full, chunk, 0);
+    if (chunk >= nchunks) break;
+    const size_t v = (size_t)chunk * 32 + lane;
+    int iters = 0, failed = 0, evals = 0;
+    if (v < nvox)
+      local_voxel(nvox, v, grain, grainR, Fin, xdir, lambda, Fp0inv, tauc_g, Swarm, Sout, dgout, Pout, dt, c,
+                  iters, evals, failed);
+    mx = max(mx, iters);
+    nf += failed;
+    si += (unsigned)iters;
+    se += (unsigned)evals;
   }
   // counters: warp-aggregated
-  const unsigned full = 0xffffffffu;
-  int mx = __reduce_max_sync(full, iters);
-  int nf = __reduce_add_sync(full, failed);
-  unsigned si = __reduce_add_sync(full, (unsigned)iters);
-  unsigned se = __reduce_add_sync(full, (unsigned)evals);
-  if ((threadIdx.x & 31) == 0) {
+  mx = __reduce_max_sync(full, mx);
+  nf = __reduce_add_sync(full, nf);
+  si = __reduce_add_sync(full, si);
+  se = __reduce_add_sync(full, se);
+  if (lane == 0) {
     if (mx) atomicMax(&counters[0], mx);
     if (nf) atomicAdd(&counters[1], nf);
     // 64-bit totals of local Newton iterations and residual evaluations (work accounting)
@@ -408,7 +443,6 @@ __global__ void __launch_bounds__(128) k_local(
     atomicAdd(&tot[1], (unsigned long long)se);
   }
 }
-
 
 // The consistent tangent at the converged S: the same work for every voxel
 // (no data-dependent iterations), so whole warps stay converged.
@@ -744,8 +778,16 @@ cudaError_t launch_hardening(const rve_s* h, cudaStream_t s) {
 }
 
 cudaError_t launch_local(const rve_s* h, double dt, double lambda, int out_buf, int warm_buf, cudaStream_t s) {
-  const unsigned blocks = (unsigned)((h->nvox + 127) / 128);
+  // persistent: as many blocks as are resident at once (no more than the chunks need)
+  static const int per_sm = [] {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_local, 128, 0) != cudaSuccess || n < 1) n = 1;
+    return n;
+  }();
+  const long need = (long)((h->nvox + 127) / 128);
+  const unsigned blocks = (unsigned)std::min<long>(need, (long)per_sm * h->num_sms);
   const double* warm = warm_buf < 0 ? h->S_c : h->S[warm_buf];
+  if (cudaError_t e = cudaMemsetAsync(h->dcount + 6, 0, sizeof(int32_t), s)) return e;
   {
     ProfScope ps_(h, RVE_K_CONSTITUTIVE, s);
     k_local<<<blocks, 128, 0, s>>>(h->nvox, h->grain, h->grainR, h->F, h->x, lambda, h->Fp0inv, h->tauc, warm,

@@ -147,7 +147,9 @@ __global__ void __launch_bounds__(256) k_fft_x_r2c(const R* __restrict__ in, V2<
   __syncthreads();
   cplx* res = block_fft<-1, R>(a, b, pl, rpb, tw);
   V2<R>* dst = spec + ((size_t)f * n2 + z) * n1 * nkx;
-  const R half = (R)0.5;
+  // the two half spectra are Z(k) +/- conj(Z(n0 - k)) without the factor 1/2
+  // of the split: every operator applied between the z passes carries it in
+  // its 1/nvox (SPEC_SCALE), exactly, as a power of two
   for (int e = threadIdx.x; e < rpb * nkx; e += blockDim.x) {
     const int jj = e / nkx, k = e - jj * nkx;
     const cplx zk = res[jj * n0 + k];
@@ -155,8 +157,8 @@ __global__ void __launch_bounds__(256) k_fft_x_r2c(const R* __restrict__ in, V2<
     const cplx zm = mk<R>(zc.x, -zc.y);
     const cplx s = add(zk, zm), d = sub(zk, zm);
     const int y0 = 2 * (j0 + jj);
-    dst[(size_t)y0 * nkx + k] = st2<R>(half * s.x, half * s.y);
-    dst[(size_t)(y0 + 1) * nkx + k] = st2<R>(half * d.y, -half * d.x);
+    dst[(size_t)y0 * nkx + k] = st2<R>(s.x, s.y);
+    dst[(size_t)(y0 + 1) * nkx + k] = st2<R>(d.y, -d.x);
   }
 }
 
@@ -228,6 +230,7 @@ __global__ void __launch_bounds__(256) k_fft_y(V2<R>* __restrict__ spec, int n1,
 }
 
 struct OpTables {
+  const double* lapw;   // OP_LAPINV weight per spectrum point, SPEC_SCALE included (FP64 path)
   const double* s20; const double* s21; const double* s22;
   const double* c20; const double* c21; const double* c22;
   const double* tan0; const double* tan1; const double* tan2;
@@ -235,27 +238,38 @@ struct OpTables {
   const double2* ph0; const double2* ph1; const double2* ph2;
 };
 
+// The forward transform leaves the spectrum at 1 / SPEC_SCALE = 2 times its
+// value (see the X pass); the operators scale by SPEC_SCALE / nvox.
+constexpr double SPEC_SCALE = 0.5;
+
+// Inverse-Laplacian weight of OP_LAPINV at one frequency, with SPEC_SCALE:
+// SPEC_SCALE / (64 nvox sum_m s2_m prod_{j!=m} c2_j), 0 where it vanishes
+__device__ __forceinline__ double lapinv_weight(const OpTables& T, double inv_nvox, int kx, int ky, int kz) {
+  const double sx = T.s20[kx], sy = T.s21[ky], sz = T.s22[kz];
+  const double cx = T.c20[kx], cy = T.c21[ky], cz = T.c22[kz];
+  const double lap = fma(sx, cy * cz, fma(cx, sy * cz, cx * cy * sz));
+  return lap > 0.0 ? (SPEC_SCALE * inv_nvox) / (64.0 * lap) : 0.0;
+}
+
 // Operator at one frequency on the three fields of a tensor row (in double).
 __device__ __forceinline__ void apply_op(const OpTables& T, const SpecParams& sp, int i, int kx, int ky, int kz,
-                                         cplx& X0, cplx& X1, cplx& X2) {
+                                         size_t kidx, cplx& X0, cplx& X1, cplx& X2) {
   cplx Y0, Y1, Y2;
+  const double sc = SPEC_SCALE * sp.inv_nvox;
   if (sp.op == OP_LAPINV) {
-    const double sx = T.s20[kx], sy = T.s21[ky], sz = T.s22[kz];
-    const double cx = T.c20[kx], cy = T.c21[ky], cz = T.c22[kz];
-    const double lap = fma(sx, cy * cz, fma(cx, sy * cz, cx * cy * sz));
-    const double w = lap > 0.0 ? sp.inv_nvox / (64.0 * lap) : 0.0;
+    const double w = T.lapw ? __ldg(T.lapw + kidx) : lapinv_weight(T, sp.inv_nvox, kx, ky, kz);
     Y0 = cscale(X0, w); Y1 = cscale(X1, w); Y2 = cscale(X2, w);
   } else if (sp.op == OP_PROJECT) {
     if (kx == 0 && ky == 0 && kz == 0) {
       if (sp.mean_out) {
-        sp.mean_out[3 * i + 0] = X0.x * sp.inv_nvox;
-        sp.mean_out[3 * i + 1] = X1.x * sp.inv_nvox;
-        sp.mean_out[3 * i + 2] = X2.x * sp.inv_nvox;
+        sp.mean_out[3 * i + 0] = X0.x * sc;
+        sp.mean_out[3 * i + 1] = X1.x * sc;
+        sp.mean_out[3 * i + 2] = X2.x * sc;
       }
       const double nv = 1.0 / sp.inv_nvox;
-      Y0 = sp.keep[3 * i + 0] ? cmk((X0.x - nv * sp.shift[3 * i + 0]) * sp.inv_nvox, X0.y * sp.inv_nvox) : cmk(0.0, 0.0);
-      Y1 = sp.keep[3 * i + 1] ? cmk((X1.x - nv * sp.shift[3 * i + 1]) * sp.inv_nvox, X1.y * sp.inv_nvox) : cmk(0.0, 0.0);
-      Y2 = sp.keep[3 * i + 2] ? cmk((X2.x - nv * sp.shift[3 * i + 2]) * sp.inv_nvox, X2.y * sp.inv_nvox) : cmk(0.0, 0.0);
+      Y0 = sp.keep[3 * i + 0] ? cmk((SPEC_SCALE * X0.x - nv * sp.shift[3 * i + 0]) * sp.inv_nvox, X0.y * sc) : cmk(0.0, 0.0);
+      Y1 = sp.keep[3 * i + 1] ? cmk((SPEC_SCALE * X1.x - nv * sp.shift[3 * i + 1]) * sp.inv_nvox, X1.y * sc) : cmk(0.0, 0.0);
+      Y2 = sp.keep[3 * i + 2] ? cmk((SPEC_SCALE * X2.x - nv * sp.shift[3 * i + 2]) * sp.inv_nvox, X2.y * sc) : cmk(0.0, 0.0);
     } else {
       const int q0 = T.nyq0[kx], q1 = T.nyq1[ky], q2 = T.nyq2[kz];
       double u0, u1, u2;
@@ -268,19 +282,19 @@ __device__ __forceinline__ void apply_op(const OpTables& T, const SpecParams& sp
         const double inv = rsqrt(fma(t0, t0, fma(t1, t1, t2 * t2)));
         u0 = t0 * inv; u1 = t1 * inv; u2 = t2 * inv;
       }
-      // (G X)_ij = u_j sum_l X_il u_l  (scaled by 1/nvox)
+      // (G X)_ij = u_j sum_l X_il u_l  (scaled by SPEC_SCALE / nvox)
       cplx s = cmk(fma(X0.x, u0, fma(X1.x, u1, X2.x * u2)), fma(X0.y, u0, fma(X1.y, u1, X2.y * u2)));
-      s = cscale(s, sp.inv_nvox);
+      s = cscale(s, sc);
       Y0 = cscale(s, u0); Y1 = cscale(s, u1); Y2 = cscale(s, u2);
     }
   } else {  // OP_CURL: G_ij = -eps_jkl D_k Fp_il
     const double2 e0 = T.ph0[kx], e1 = T.ph1[ky], e2 = T.ph2[kz];
     const cplx p0 = cmk(1.0 + e0.x, e0.y), p1 = cmk(1.0 + e1.x, e1.y), p2 = cmk(1.0 + e2.x, e2.y);
     const cplx m0 = cmk(e0.x - 1.0, e0.y), m1 = cmk(e1.x - 1.0, e1.y), m2 = cmk(e2.x - 1.0, e2.y);
-    const double sc = sp.inv4h * sp.inv_nvox;
-    const cplx D0 = cscale(cmul(m0, cmul(p1, p2)), sc);
-    const cplx D1 = cscale(cmul(p0, cmul(m1, p2)), sc);
-    const cplx D2 = cscale(cmul(p0, cmul(p1, m2)), sc);
+    const double scd = sp.inv4h * sc;
+    const cplx D0 = cscale(cmul(m0, cmul(p1, p2)), scd);
+    const cplx D1 = cscale(cmul(p0, cmul(m1, p2)), scd);
+    const cplx D2 = cscale(cmul(p0, cmul(p1, m2)), scd);
     Y0 = csub(cmul(D2, X1), cmul(D1, X2));
     Y1 = csub(cmul(D0, X2), cmul(D2, X0));
     Y2 = csub(cmul(D1, X0), cmul(D0, X1));
@@ -288,12 +302,23 @@ __device__ __forceinline__ void apply_op(const OpTables& T, const SpecParams& sp
   X0 = Y0; X1 = Y1; X2 = Y2;
 }
 
-// inverse-Laplacian weight in float for the float path
-__device__ __forceinline__ float lapinv_weight_f(const OpTables& T, float inv_nvox, int kx, int ky, int kz) {
+// inverse-Laplacian weight in float for the float path (SPEC_SCALE included
+// through the caller's scale)
+__device__ __forceinline__ float lapinv_weight_f(const OpTables& T, float scale, int kx, int ky, int kz) {
   const float sx = (float)T.s20[kx], sy = (float)T.s21[ky], sz = (float)T.s22[kz];
   const float cx = (float)T.c20[kx], cy = (float)T.c21[ky], cz = (float)T.c22[kz];
   const float lap = fmaf(sx, cy * cz, fmaf(cx, sy * cz, cx * cy * sz));
-  return lap > 0.0f ? inv_nvox / (64.0f * lap) : 0.0f;
+  return lap > 0.0f ? scale / (64.0f * lap) : 0.0f;
+}
+
+// the OP_LAPINV weight of every spectrum point (layout of one field's half
+// spectrum, [kz][ky][kx]), built once per handle
+__global__ void k_lapinv_table(double* __restrict__ w, OpTables T, int nkx, int n1, int n2, double inv_nvox) {
+  const size_t n = (size_t)nkx * n1 * n2;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int kx = (int)(e % nkx), ky = (int)((e / nkx) % n1), kz = (int)(e / ((size_t)nkx * n1));
+    w[e] = lapinv_weight(T, inv_nvox, kx, ky, kz);
+  }
 }
 
 // ---------------------------------------------------------------- pass Z + operator
@@ -321,7 +346,7 @@ __global__ void __launch_bounds__(256) k_fft_z_op(V2<R>* __restrict__ spec, int 
   __syncthreads();
   cx* res = block_fft<-1, R>(a, b, pl, 3 * tx, tw);
   cx* oth = (res == a) ? b : a;
-  const float inv_nvox_f = (float)sp.inv_nvox;
+  const float inv_nvox_f = (float)(SPEC_SCALE * sp.inv_nvox);
   for (int e = threadIdx.x; e < tx * n2; e += blockDim.x) {
     const int t = e / n2, z = e - t * n2;
     const int kx = kx0 + t;
@@ -335,7 +360,7 @@ __global__ void __launch_bounds__(256) k_fft_z_op(V2<R>* __restrict__ spec, int 
     } else {
       cplx X0 = cmk((double)Y0.x, (double)Y0.y), X1 = cmk((double)Y1.x, (double)Y1.y),
            X2 = cmk((double)Y2.x, (double)Y2.y);
-      apply_op(T, sp, i, kx, ky, z, X0, X1, X2);
+      apply_op(T, sp, i, kx, ky, z, ((size_t)z * gridDim.y + ky) * nkx + kx, X0, X1, X2);
       Y0 = mk<R>((R)X0.x, (R)X0.y); Y1 = mk<R>((R)X1.x, (R)X1.y); Y2 = mk<R>((R)X2.x, (R)X2.y);
     }
     oth[(0 * tx + t) * n2 + z] = Y0;
@@ -395,6 +420,7 @@ int threads_for(int elems) {
 
 OpTables op_tables(const rve_s* h) {
   OpTables T;
+  T.lapw = h->lapw;
   T.tan0 = h->ax[0].tanh_; T.tan1 = h->ax[1].tanh_; T.tan2 = h->ax[2].tanh_;
   T.nyq0 = h->ax[0].nyq; T.nyq1 = h->ax[1].nyq; T.nyq2 = h->ax[2].nyq;
   T.ph0 = h->ax[0].ph; T.ph1 = h->ax[1].ph; T.ph2 = h->ax[2].ph;
@@ -451,7 +477,7 @@ cudaError_t inv(const rve_s* h, R* out, cudaStream_t s, const double* done, int 
   dim3 gy((h->nkx + ty - 1) / ty, h->n2, nf);
   size_t shy = 2 * (size_t)ty * h->n1 * sizeof(CX<R>);
   {
-    ProfScope ps_(h, h->fft_cat >= 0 ? h->fft_cat : RVE_K_FFT_Y, s);
+    ProfScope ps_(h, h->fft_cat >= 0 ? h->fft_cat : RVE_K_FFT_Y_INV, s);
     k_fft_y<+1, R><<<gy, threads_for(ty * h->n1), shy, s>>>(spect<R>(h), h->n1, h->n2, h->nkx, ty,
                                                             to_dev(h->plan[1]), twt<R>(h, 1), done);
   }
@@ -467,6 +493,12 @@ cudaError_t inv(const rve_s* h, R* out, cudaStream_t s, const double* done, int 
 }
 
 }  // namespace
+
+cudaError_t launch_lapinv_table(const rve_s* h, cudaStream_t s) {
+  if (!h->lapw) return cudaSuccess;
+  k_lapinv_table<<<RVE_RED_BLOCKS, 256, 0, s>>>(h->lapw, op_tables(h), h->nkx, h->n1, h->n2, 1.0 / (double)h->nvox);
+  return cudaGetLastError();
+}
 
 void make_plan(int n, FFTPlan* p) {
   p->n = n;

@@ -103,6 +103,7 @@ void carve(rve_s* h, Carver& c) {
   h->bv = c.take<double>(9 * nv);
   h->bs = c.take<double>(9 * nv);
   h->spec = c.take<double2>(9 * h->nspec);
+  h->lapw = c.take<double>(h->nspec);
   if (h->opt.precision == 1) {
     for (int a = 0; a < 3; ++a) h->ax[a].tw32 = c.take<float2>(ns[a]);
     h->spec32 = c.take<float2>(3 * h->nspec);
@@ -910,6 +911,7 @@ rve_status rve_create(const int32_t* grain_id, int n0, int n1, int n2, const dou
             bad(cudaMemsetAsync(h->nye, 0, 9 * nvox * sizeof(double), s)) ||
             bad(cudaMemsetAsync(h->dscal, 0, 64 * sizeof(double), s)) ||
             bad(cudaMemsetAsync(h->dcount, 0, 16 * sizeof(int32_t), s)) ||
+            bad(launch_lapinv_table(h, s)) ||
             bad(cudaStreamSynchronize(s));
   }
   if (!fail_ && opt->autotune) fail_ = autotune(h) != RVE_OK;

@@ -148,12 +148,14 @@ struct rve_s {
   double *R, *x, *r, *p, *t, *q;
   double *bv, *bs;      // BiCGStab vectors v and s
   double2* spec;        // 9 * nspec
+  double* lapw;         // nspec: inverse-Laplacian weight of the projection's Laplace solve
   // mixed precision (precision == 1): FP32 conjugate-gradient state
   float2* spec32;       // 3 * nspec
   float *x32, *r32, *p32, *t32, *du32;   // 9, 9, 9, 9, 6 components
   double* partial;      // 4 * RVE_RED_BLOCKS
   double* dscal;        // device scalars (see DS_*)
-  int32_t* dcount;      // device counters: [0] local max iters, [1] local failures, [4] last-block ticket
+  int32_t* dcount;      // device counters: [0] local max iters, [1] local failures, [4] last-block ticket,
+                        // [6] next voxel chunk of the local update, [8..11] 64-bit work totals
   double* hscal;        // pinned host mirror of dscal
   int32_t* hcount;      // pinned host mirror of dcount
 
@@ -191,6 +193,8 @@ cudaError_t launch_fft_op(const rve_s* h, const SpecParams& sp, cudaStream_t s, 
 cudaError_t launch_fft_inverse(const rve_s* h, double* out, cudaStream_t s, const double* done = nullptr,
                                int nf = 9);
 void make_plan(int n, FFTPlan* p);
+// fills h->lapw (once, at create)
+cudaError_t launch_lapinv_table(const rve_s* h, cudaStream_t s);
 cudaError_t launch_fft_forward32(const rve_s* h, const float* in, cudaStream_t s, const double* done);
 cudaError_t launch_fft_lapinv32(const rve_s* h, const SpecParams& sp, cudaStream_t s, const double* done);
 cudaError_t launch_fft_inverse32(const rve_s* h, float* out, cudaStream_t s, const double* done);
