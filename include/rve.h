@@ -109,6 +109,14 @@ typedef struct {
   int32_t stencils;      /* divergence and gradient stencils of the projection: 0 row strips (one
                             warp per x line, separable, no halo) where n0 is 32, 64, 96 or 128, else
                             tiles; 1 tiles always.  Equal results to round-off. */
+  int32_t continuation;  /* 0..6: when Newton-Raphson fails on an increment (RVE_ENOCONV_NEWTON,
+                            _CG or _LOCAL), solve the same increment again from its start with the
+                            macroscopic load in 2^k equal stages, k = 1 .. continuation, each stage
+                            starting from the previous one's solution.  The hardening stays frozen
+                            over the increment and the last stage solves its own equations: the
+                            converged increment is the same, only the path to it differs.  With
+                            continuation > 0 the direct solve is given max(8, max_newton / 4)
+                            iterations, each stage max_newton. */
 } rve_options;
 
 #define RVE_MAX_NEWTON_LOG 64
@@ -120,6 +128,7 @@ typedef struct {
   int32_t local_failures;
   int32_t halvings;
   int32_t bicgstab_solves;                      /* Newton steps solved by BiCGStab */
+  int32_t load_stages;                          /* 1, or the stages of the load continuation that solved it */
   int64_t local_iters_total;                    /* local Newton iterations summed over voxels and evaluations */
   int64_t local_evals_total;                    /* local residual evaluations, likewise */
   double residual;                              /* final relative residual */
@@ -223,6 +232,15 @@ rve_status rve_set_fields(rve_t* rve, uint32_t which, const void* src, size_t by
  *     may alias) under the given strain mask (zero mode: components with
  *     strain_mask[c] == 0 kept, the others zeroed). */
 rve_status rve_eval_hardening(rve_t* rve);
+/* Nye tensor of the committed Fp alone (field NYE), G_ij = -eps_jkl d_k Fp_il,
+ * with the derivative of scheme 0: the rotated-scheme discrete derivative the
+ * method uses (App. A Eq. kas, App. B Eq. nyeindexfourier), or 1: the
+ * standard spectral derivative i xi_k / h (the continuous frequencies App. A
+ * contrasts it with; 0 at the Nyquist frequency), which rings (Gibbs
+ * oscillations) where Fp jumps across a grain boundary (App. B).  The
+ * hardening fields are left as they were.  Errors: RVE_EINVAL for another
+ * scheme. */
+rve_status rve_eval_nye(rve_t* rve, int scheme);
 rve_status rve_eval_constitutive(rve_t* rve, double dt, int32_t* local_max_iters, int32_t* local_failures);
 rve_status rve_project(rve_t* rve, const uint8_t strain_mask[9], const double* d_X, double* d_Y);
 

@@ -17,6 +17,8 @@ Axis convention: a field array has numpy shape (n2, n1, n0, ...) so that x
 * Nye tensor (Eq. Nye_finite_strain, App. B): the reading used is
   G_ij = - eps_jkl d_k Fp_il  (i: Burgers index = row of Fp, j: line index),
   consistent with G_ij = sum_a rho^a b_i^a t_j^a (Eq. defA).
+* Standard spectral derivative (i xi / h, App. A's continuous frequencies),
+  for the Nye tensor only, to show the Gibbs oscillations of App. B.
 * Galerkin projection with mixed control (Sec. 2.2, Eqs. weakarbi,
   eql_discrete2): for xi != 0 the compatible projection
   (G X)^_ij = D_j sum_l X^_il conj(D_l) / sum_m |D_m|^2 with D the derivative
@@ -61,6 +63,30 @@ def stencil_derivative(f, axis, h):
 def nye_tensor(Fp, h):
     """G_ij = - eps_jkl d_k Fp_il for Fp of shape (n2, n1, n0, 3, 3)."""
     dFp = np.stack([stencil_derivative(Fp, k, h) for k in range(3)], axis=-1)  # [..., i, l, k]
+    return -np.einsum("jkl,...ilk->...ij", LEVI, dFp)
+
+
+def standard_frequencies(n):
+    """xi = 2 pi fftfreq(n), with the Nyquist entry of an even n set to 0 (its
+    derivative has no real representation): the continuous frequencies that
+    App. A contrasts with the rotated scheme."""
+    xi = 2.0 * np.pi * np.fft.fftfreq(n)
+    if n % 2 == 0:
+        xi[n // 2] = 0.0
+    return xi
+
+
+def nye_tensor_standard(Fp, h):
+    """G_ij = - eps_jkl d_k Fp_il with the standard spectral derivative
+    d_k <-> i xi_k / h (the trigonometric interpolant's derivative), for the
+    comparison of App. B: at a jump of Fp across a grain boundary it rings
+    (Gibbs oscillations), where the rotated stencil of nye_tensor stays local."""
+    n2, n1, n0 = Fp.shape[:3]
+    Fh = np.fft.fftn(Fp, axes=(0, 1, 2))
+    xs = (standard_frequencies(n0)[None, None, :], standard_frequencies(n1)[None, :, None],
+          standard_frequencies(n2)[:, None, None])
+    dFp = np.stack([np.real(np.fft.ifftn(1j * xs[k][..., None, None] / h * Fh, axes=(0, 1, 2)))
+                    for k in range(3)], axis=-1)                              # [..., i, l, k]
     return -np.einsum("jkl,...ilk->...ij", LEVI, dFp)
 
 

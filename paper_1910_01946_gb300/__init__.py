@@ -45,13 +45,15 @@ class rve_options(C.Structure):
                 ("local_tol", C.c_double), ("max_newton", C.c_int32), ("max_cg", C.c_int32),
                 ("max_local", C.c_int32), ("max_halvings", C.c_int32), ("extrapolate", C.c_int32),
                 ("precision", C.c_int32), ("cg_adaptive", C.c_int32), ("krylov", C.c_int32),
-                ("graphs", C.c_int32), ("tma", C.c_int32), ("autotune", C.c_int32), ("stencils", C.c_int32)]
+                ("graphs", C.c_int32), ("tma", C.c_int32), ("autotune", C.c_int32), ("stencils", C.c_int32),
+                ("continuation", C.c_int32)]
 
 
 class rve_step_info(C.Structure):
     _fields_ = [("converged", C.c_int32), ("newton_iters", C.c_int32), ("cg_iters_total", C.c_int32),
                 ("local_max_iters", C.c_int32), ("local_failures", C.c_int32), ("halvings", C.c_int32),
-                ("bicgstab_solves", C.c_int32), ("local_iters_total", C.c_int64), ("local_evals_total", C.c_int64),
+                ("bicgstab_solves", C.c_int32), ("load_stages", C.c_int32), ("local_iters_total", C.c_int64),
+                ("local_evals_total", C.c_int64),
                 ("residual", C.c_double), ("seconds", C.c_double), ("cg_iters", C.c_int32 * MAX_NEWTON_LOG),
                 ("residuals", C.c_double * (MAX_NEWTON_LOG + 1))]
 
@@ -69,6 +71,7 @@ _SIGS = {
     "rve_get_fields": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.c_size_t, C.c_int]),
     "rve_set_fields": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.c_size_t, C.c_int]),
     "rve_eval_hardening": (C.c_int, [C.c_void_p]),
+    "rve_eval_nye": (C.c_int, [C.c_void_p, C.c_int]),
     "rve_eval_constitutive": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "rve_project": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rve_checkpoint_bytes": (C.c_size_t, [C.c_void_p]),
@@ -248,7 +251,7 @@ def rve_destroy(h):
 # ---- handle wrapper ---------------------------------------------------------
 DEFAULT_OPTIONS = dict(newton_tol=1e-11, cg_tol=1e-11, local_tol=1e-14, max_newton=100, max_cg=2000,
                        max_local=60, max_halvings=12, extrapolate=1, precision=0, cg_adaptive=1, krylov=0, graphs=1, tma=1, autotune=0,
-                       stencils=0)
+                       stencils=0, continuation=2)
 
 
 def make_material(m) -> rve_material:
@@ -332,7 +335,7 @@ class RVE:
                    cg_iters_total=info.cg_iters_total, local_max_iters=info.local_max_iters,
                    local_failures=info.local_failures, halvings=info.halvings, residual=info.residual,
                    local_iters_total=info.local_iters_total, local_evals_total=info.local_evals_total,
-                   bicgstab_solves=info.bicgstab_solves,
+                   bicgstab_solves=info.bicgstab_solves, load_stages=info.load_stages,
                    residuals=list(info.residuals[:min(info.newton_iters, MAX_NEWTON_LOG) + 1]),
                    seconds=info.seconds)
         if check:
@@ -399,6 +402,11 @@ class RVE:
 
     def eval_hardening(self):
         self._check(rve_eval_hardening(self.h), "rve_eval_hardening")
+
+    def eval_nye(self, scheme=0):
+        """Nye tensor of the committed Fp into field NYE: scheme 0 rotated (the
+        method's), 1 standard spectral derivative (for comparison)."""
+        self._check(load_library().rve_eval_nye(self.h, int(scheme)), "rve_eval_nye")
 
     def eval_constitutive(self, dt):
         st, it, nf = rve_eval_constitutive(self.h, float(dt))

@@ -236,6 +236,7 @@ struct OpTables {
   const double* tan0; const double* tan1; const double* tan2;
   const int8_t* nyq0; const int8_t* nyq1; const int8_t* nyq2;
   const double2* ph0; const double2* ph1; const double2* ph2;
+  const double* xi0; const double* xi1; const double* xi2;
 };
 
 // The forward transform leaves the spectrum at 1 / SPEC_SCALE = 2 times its
@@ -287,6 +288,13 @@ __device__ __forceinline__ void apply_op(const OpTables& T, const SpecParams& sp
       s = cscale(s, sc);
       Y0 = cscale(s, u0); Y1 = cscale(s, u1); Y2 = cscale(s, u2);
     }
+  } else if (sp.op == OP_CURL_STD) {
+    // the standard spectral derivative i xi_k / h (no rotated stencil)
+    const double scd = 4.0 * sp.inv4h * sc;
+    const cplx D0 = cmk(0.0, T.xi0[kx] * scd), D1 = cmk(0.0, T.xi1[ky] * scd), D2 = cmk(0.0, T.xi2[kz] * scd);
+    Y0 = csub(cmul(D2, X1), cmul(D1, X2));
+    Y1 = csub(cmul(D0, X2), cmul(D2, X0));
+    Y2 = csub(cmul(D1, X0), cmul(D0, X1));
   } else {  // OP_CURL: G_ij = -eps_jkl D_k Fp_il
     const double2 e0 = T.ph0[kx], e1 = T.ph1[ky], e2 = T.ph2[kz];
     const cplx p0 = cmk(1.0 + e0.x, e0.y), p1 = cmk(1.0 + e1.x, e1.y), p2 = cmk(1.0 + e2.x, e2.y);
@@ -424,6 +432,7 @@ OpTables op_tables(const rve_s* h) {
   T.tan0 = h->ax[0].tanh_; T.tan1 = h->ax[1].tanh_; T.tan2 = h->ax[2].tanh_;
   T.nyq0 = h->ax[0].nyq; T.nyq1 = h->ax[1].nyq; T.nyq2 = h->ax[2].nyq;
   T.ph0 = h->ax[0].ph; T.ph1 = h->ax[1].ph; T.ph2 = h->ax[2].ph;
+  T.xi0 = h->ax[0].xi; T.xi1 = h->ax[1].xi; T.xi2 = h->ax[2].xi;
   T.s20 = h->ax[0].s2; T.s21 = h->ax[1].s2; T.s22 = h->ax[2].s2;
   T.c20 = h->ax[0].c2; T.c21 = h->ax[1].c2; T.c22 = h->ax[2].c2;
   return T;

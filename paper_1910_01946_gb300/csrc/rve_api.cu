@@ -74,6 +74,7 @@ void carve(rve_s* h, Carver& c) {
     h->ax[a].ph = c.take<double2>(ns[a]);
     h->ax[a].s2 = c.take<double>(ns[a]);
     h->ax[a].c2 = c.take<double>(ns[a]);
+    h->ax[a].xi = c.take<double>(ns[a]);
   }
   h->F_c = c.take<double>(9 * nv);
   h->Fp = c.take<double>(9 * nv);
@@ -781,7 +782,8 @@ rve_status rve_create(const int32_t* grain_id, int n0, int n1, int n2, const dou
         mat->K > 0 && mat->yc >= 0 && mat->rho0_total > 0 && mat->tau0 >= 0 && mat->alpha >= 0 &&
         mat->q[0] > 0 && opt->L > 0 && opt->newton_tol > 0 && opt->cg_tol > 0 && opt->local_tol > 0 &&
         opt->max_newton > 0 && opt->max_cg > 0 && opt->max_local > 0 && opt->max_halvings >= 0 &&
-        opt->krylov >= 0 && opt->krylov <= 2 && (opt->stencils == 0 || opt->stencils == 1)))
+        opt->krylov >= 0 && opt->krylov <= 2 && (opt->stencils == 0 || opt->stencils == 1) &&
+        opt->continuation >= 0 && opt->continuation <= 6))
     return RVE_EINVAL;
   const size_t nvox = (size_t)n0 * n1 * n2;
   for (size_t v = 0; v < nvox; ++v)
@@ -846,12 +848,13 @@ rve_status rve_create(const int32_t* grain_id, int n0, int n1, int n2, const dou
   build_tables(*mat, q, Ap, screw);
   const int ns[3] = {n0, n1, n2};
   std::vector<double2> tw[3], ph[3];
-  std::vector<double> tn[3], s2[3], c2[3];
+  std::vector<double> tn[3], s2[3], c2[3], xi[3];
   std::vector<int8_t> nq[3];
   const double PI = 3.14159265358979323846;
   for (int a = 0; a < 3; ++a) {
     const int n = ns[a];
     tw[a].resize(n); ph[a].resize(n); tn[a].resize(n); nq[a].resize(n); s2[a].resize(n); c2[a].resize(n);
+    xi[a].resize(n);
     for (int t = 0; t < n; ++t) {
       const double ang = 2.0 * PI * (double)t / n;
       tw[a][t] = make_double2(std::cos(ang), -std::sin(ang));
@@ -863,6 +866,7 @@ rve_status rve_create(const int32_t* grain_id, int n0, int n1, int n2, const dou
       const double sh = std::sin(PI * (double)t / n), chf = std::cos(PI * (double)t / n);
       s2[a][t] = nyq ? 1.0 : (t == 0 ? 0.0 : sh * sh);     // sin^2(xi/2), xi = 2 pi t / n
       c2[a][t] = nyq ? 0.0 : (t == 0 ? 1.0 : chf * chf);   // cos^2(xi/2)
+      xi[a][t] = nyq ? 0.0 : 2.0 * PI * (double)ks / n;     // standard frequency
     }
     // exact values at the quarter points
     for (int t = 0; t < n; ++t) {
@@ -885,7 +889,8 @@ rve_status rve_create(const int32_t* grain_id, int n0, int n1, int n2, const dou
             bad(cudaMemcpyAsync((void*)h->ax[a].nyq, nq[a].data(), ns[a] * sizeof(int8_t), cudaMemcpyHostToDevice, s)) ||
             bad(cudaMemcpyAsync((void*)h->ax[a].ph, ph[a].data(), ns[a] * sizeof(double2), cudaMemcpyHostToDevice, s)) ||
             bad(cudaMemcpyAsync((void*)h->ax[a].s2, s2[a].data(), ns[a] * sizeof(double), cudaMemcpyHostToDevice, s)) ||
-            bad(cudaMemcpyAsync((void*)h->ax[a].c2, c2[a].data(), ns[a] * sizeof(double), cudaMemcpyHostToDevice, s));
+            bad(cudaMemcpyAsync((void*)h->ax[a].c2, c2[a].data(), ns[a] * sizeof(double), cudaMemcpyHostToDevice, s)) ||
+            bad(cudaMemcpyAsync((void*)h->ax[a].xi, xi[a].data(), ns[a] * sizeof(double), cudaMemcpyHostToDevice, s));
     if (!fail_ && h->opt.precision == 1) {
       std::vector<float2> t32(ns[a]);
       for (int t = 0; t < ns[a]; ++t) t32[t] = make_float2((float)tw[a][t].x, (float)tw[a][t].y);
@@ -925,6 +930,125 @@ rve_status rve_create(const int32_t* grain_id, int n0, int n1, int n2, const dou
   return RVE_OK;
 }
 
+// Newton-Raphson on the equilibrium G*(P(F) - Pbar) = 0 of one increment
+// (Sec. 2.2, Eq. linequil2ast) from the iterate in h->F, with the hardening
+// of the increment frozen.  The first local evaluation is warm-started from
+// S[warm] (the committed S when warm < 0).  On RVE_OK h->cur holds the
+// converged evaluation.  Iteration counts accumulate into loc.
+static rve_status newton_solve(rve_s* h, double dt, const uint8_t* mask, const double* Pb, int warm,
+                               rve_step_info& loc, int max_iters) {
+  int cur = warm < 0 ? 0 : 1 - warm;
+  double rabs, scale;
+  int lmax, lfail;
+  h->cur = cur;
+  rve_status st = eval_residual(h, dt, 0.0, cur, warm, mask, Pb, &rabs, &scale, &lmax, &lfail);
+  if (st != RVE_OK) return st;
+  loc.local_max_iters = std::max(loc.local_max_iters, lmax);
+  loc.local_failures = lfail;
+  double res = rabs / scale;
+  if (loc.newton_iters <= RVE_MAX_NEWTON_LOG) loc.residuals[loc.newton_iters] = res;
+  int it = 0;
+  for (;;) {
+    loc.residual = res;
+    // a non-finite value anywhere in the state or the load path poisons the
+    // residual; it is reported as such even though the local update at the
+    // voxels concerned also fails
+    if (!std::isfinite(res)) return (fail(h, RVE_ENAN, "non-finite residual"));
+    if (lfail) return (fail(h, RVE_ENOCONV_LOCAL, "local update did not converge"));
+    if (res <= h->opt.newton_tol) break;
+    if (it >= max_iters) return fail(h, RVE_ENOCONV_NEWTON, "Newton-Raphson reached its iteration limit");
+    // the tangent is built only at iterates that get a Krylov solve: not at
+    // rejected line-search trials, not at the iterate that ends the increment
+    if (cudaError_t e = launch_tangent(h, dt, 0.0, cur, h->stream)) {
+      h->err = cudaGetErrorString(e);
+      return RVE_ECUDA;
+    }
+    int ncg = 0;
+    bool cgok = false;
+    // inexact Newton: with cg_adaptive the linear solve only needs to be as
+    // accurate as the current residual (forcing term min(1e-2, res)); the
+    // converged increment does not depend on it
+    const double eta = h->opt.cg_adaptive ? std::fmax(h->opt.cg_tol, std::fmin(1e-2, res)) : h->opt.cg_tol;
+    double lam = 1.0, rt = 0.0, sct = 0.0;
+    int lm = 0, lf = 0;
+    bool acc = false;
+    // krylov 0: conjugate gradients (the paper's solver); when no step along
+    // the CG direction lowers the residual, the iteration is solved again with
+    // BiCGStab.  A CG solve cut off at max_cg still gives its direction a line
+    // search first: the truncated iterate is a damped step (CG iterates grow in
+    // norm from zero), which on an ill-conditioned tangent often does better
+    // than a fully solved BiCGStab step.  1: BiCGStab only; 2: CG only.
+    const int attempts = h->opt.krylov == 0 ? 2 : 1;
+    for (int att = 0; att < attempts && !acc; ++att) {
+      const bool use_bicg = h->opt.krylov == 1 || att == 1;
+      if (use_bicg) {
+        // trials of the rejected CG line search overwrote R: rebuild it from
+        // the current iterate's stress (its tangent K[cur] is untouched)
+        if (att == 1) RVE_TRY(run_project_stencil(h, h->P[cur], h->R, mask, Pb));
+        st = bicgstab_solve(h, mask, h->opt.precision == 1 ? std::fmax(eta, 1e-10) : eta, &ncg, &cgok);
+        ++loc.bicgstab_solves;
+      } else {
+        st = h->opt.precision == 1 ? cg_solve32(h, mask, eta, &ncg, &cgok) : cg_solve(h, mask, eta, &ncg, &cgok);
+      }
+      if (st != RVE_OK) return st;
+      // dF has zero strain-controlled means by construction (every Krylov vector
+      // is a projection); remove what round-off left there, which a long or
+      // stalled solve with a large dF would otherwise carry into <F>
+      RVE_CUDA(h, launch_zero_means(h, h->x, 0x1FFu & ~kept_means(mask), h->stream));
+      if (loc.newton_iters < RVE_MAX_NEWTON_LOG) loc.cg_iters[loc.newton_iters] += ncg;
+      loc.cg_iters_total += ncg;
+      // backtracking on phi(lam) = rms(R(F + lam dF))^2 with sufficient decrease;
+      // after a rejected trial the next lam minimises the quadratic through
+      // phi(0), the Newton slope -2 phi(0) and phi(lam), kept in [0.1, 0.5] lam.
+      // A trial at which some voxel's local update fails (the step asks for
+      // slips above the local cap) is halved on a budget of its own: the
+      // current iterate itself has a converged local state, so a small enough
+      // step always passes.
+      lam = 1.0;
+      const double f0 = rabs * rabs;
+      int shrink = 0, local_cuts = 0;
+      while (shrink <= h->opt.max_halvings && local_cuts <= 40) {
+        st = eval_residual(h, dt, lam, 1 - cur, cur, mask, Pb, &rt, &sct, &lm, &lf);
+        if (st != RVE_OK) return st;
+        if (lf == 0 && rt < rabs * (1.0 - 1e-4 * lam)) { acc = true; break; }
+        double next = 0.5 * lam;
+        if (lf == 0 && std::isfinite(rt)) {
+          const double c = (rt * rt - f0 * (1.0 - 2.0 * lam)) / (lam * lam);
+          if (c > 0.0) next = std::fmin(std::fmax(f0 / c, 0.1 * lam), 0.5 * lam);
+          ++shrink;
+        } else {
+          ++local_cuts;
+        }
+        lam = next;
+        ++loc.halvings;
+      }
+    }
+    if (!acc) {
+      if (lf) return (fail(h, RVE_ENOCONV_LOCAL, "local update did not converge in the line search"));
+      if (!cgok) return (fail(h, RVE_ENOCONV_CG, "the Krylov solve did not converge"));
+      return (fail(h, RVE_ENOCONV_NEWTON, "no step along the Newton direction lowers the residual"));
+    }
+    if (cudaError_t e = launch_axpy_F(h, lam, h->stream)) {
+      h->err = cudaGetErrorString(e);
+      return RVE_ECUDA;
+    }
+    cur = 1 - cur;
+    h->cur = cur;
+    rabs = rt;
+    res = rt / sct;
+    loc.local_max_iters = lm > loc.local_max_iters ? lm : loc.local_max_iters;
+    ++loc.newton_iters;
+    ++it;
+    if (loc.newton_iters <= RVE_MAX_NEWTON_LOG) loc.residuals[loc.newton_iters] = res;
+  }
+  return RVE_OK;
+}
+
+// statuses after which the increment is tried again with the load in stages
+static bool retryable(rve_status st) {
+  return st == RVE_ENOCONV_NEWTON || st == RVE_ENOCONV_CG || st == RVE_ENOCONV_LOCAL;
+}
+
 rve_status rve_step(rve_t* h, const double dFbar[9], const uint8_t strain_mask[9], const double Pbar[9], double dt,
                     rve_step_info* info) {
   if (!h || !dFbar || !strain_mask || !Pbar || !(dt > 0) || !std::isfinite(dt)) return RVE_EINVAL;
@@ -959,109 +1083,42 @@ rve_status rve_step(rve_t* h, const double dFbar[9], const uint8_t strain_mask[9
     h->err = cudaGetErrorString(e);
     return finish(RVE_ECUDA);
   }
-  int cur = 0;
-  double rabs, scale;
-  int lmax, lfail;
-  h->cur = cur;
-  st = eval_residual(h, dt, 0.0, cur, -1, mask, Pb, &rabs, &scale, &lmax, &lfail);
-  if (st != RVE_OK) return finish(st);
-  loc.local_max_iters = lmax;
-  loc.local_failures = lfail;
-  double res = rabs / scale;
-  loc.residuals[0] = res;
-  for (;;) {
-    loc.residual = res;
-    // a non-finite value anywhere in the state or the load path poisons the
-    // residual; it is reported as such even though the local update at the
-    // voxels concerned also fails
-    if (!std::isfinite(res)) return finish(fail(h, RVE_ENAN, "non-finite residual"));
-    if (lfail) return finish(fail(h, RVE_ENOCONV_LOCAL, "local update did not converge"));
-    if (res <= h->opt.newton_tol) break;
-    if (loc.newton_iters >= h->opt.max_newton)
-      return finish(fail(h, RVE_ENOCONV_NEWTON, "Newton-Raphson reached max_newton"));
-    // the tangent is built only at iterates that get a Krylov solve: not at
-    // rejected line-search trials, not at the iterate that ends the increment
-    if (cudaError_t e = launch_tangent(h, dt, 0.0, cur, h->stream)) {
-      h->err = cudaGetErrorString(e);
-      return finish(RVE_ECUDA);
-    }
-    int ncg = 0;
-    bool cgok = false;
-    // inexact Newton: with cg_adaptive the linear solve only needs to be as
-    // accurate as the current residual (forcing term min(1e-2, res)); the
-    // converged increment does not depend on it
-    const double eta = h->opt.cg_adaptive ? std::fmax(h->opt.cg_tol, std::fmin(1e-2, res)) : h->opt.cg_tol;
-    double lam = 1.0, rt = 0.0, sct = 0.0;
-    int lm = 0, lf = 0;
-    bool acc = false;
-    // krylov 0: conjugate gradients (the paper's solver); when no step along
-    // the CG direction lowers the residual, the iteration is solved again with
-    // BiCGStab.  A CG solve cut off at max_cg still gives its direction a line
-    // search first: the truncated iterate is a damped step (CG iterates grow in
-    // norm from zero), which on an ill-conditioned tangent often does better
-    // than a fully solved BiCGStab step.  1: BiCGStab only; 2: CG only.
-    const int attempts = h->opt.krylov == 0 ? 2 : 1;
-    for (int att = 0; att < attempts && !acc; ++att) {
-      const bool use_bicg = h->opt.krylov == 1 || att == 1;
-      if (use_bicg) {
-        // trials of the rejected CG line search overwrote R: rebuild it from
-        // the current iterate's stress (its tangent K[cur] is untouched)
-        if (att == 1) RVE_TRY(run_project_stencil(h, h->P[cur], h->R, mask, Pb));
-        st = bicgstab_solve(h, mask, h->opt.precision == 1 ? std::fmax(eta, 1e-10) : eta, &ncg, &cgok);
-        ++loc.bicgstab_solves;
+  // with continuation available, the direct solve gets a quarter of max_newton
+  // (at least 8): an increment that needs more goes to the staged load at once
+  const int direct_max = h->opt.continuation > 0 ? std::max(8, h->opt.max_newton / 4) : h->opt.max_newton;
+  st = newton_solve(h, dt, mask, Pb, -1, loc, std::min(direct_max, h->opt.max_newton));
+  loc.load_stages = 1;
+  // Load continuation: when Newton fails on the increment (typically at the
+  // plastic onset of a large, strongly non-linear RVE), the same increment is
+  // solved again from its start with the macroscopic load applied in 2^k equal
+  // stages (k = 1 .. continuation), each stage's solution the starting point
+  // of the next.  The hardening stays frozen and the last stage solves the
+  // increment's own equations, so the converged increment is the same; only
+  // the path to it changes.
+  for (int lev = 1; retryable(st) && lev <= h->opt.continuation; ++lev) {
+    const int nst = 1 << lev;
+    loc.load_stages = nst;
+    st = RVE_OK;
+    for (int k = 1; k <= nst && st == RVE_OK; ++k) {
+      const double th = (double)k / nst;
+      double dFs[9], Ps[9];
+      for (int c = 0; c < 9; ++c) { dFs[c] = dFb[c] / nst; Ps[c] = th * Pb[c]; }
+      cudaError_t e;
+      if (k == 1) {
+        double dF1[9];
+        for (int c = 0; c < 9; ++c) dF1[c] = th * dFb[c];
+        e = launch_predictor(h, dF1, h->dFbar_prev, th * ratio, extrap, h->stream);
       } else {
-        st = h->opt.precision == 1 ? cg_solve32(h, mask, eta, &ncg, &cgok) : cg_solve(h, mask, eta, &ncg, &cgok);
+        e = launch_shift_F(h, dFs, h->stream);
       }
-      if (st != RVE_OK) return finish(st);
-      // dF has zero strain-controlled means by construction (every Krylov vector
-      // is a projection); remove what round-off left there, which a long or
-      // stalled solve with a large dF would otherwise carry into <F>
-      RVE_CUDA(h, launch_zero_means(h, h->x, 0x1FFu & ~kept_means(mask), h->stream));
-      if (loc.newton_iters < RVE_MAX_NEWTON_LOG) loc.cg_iters[loc.newton_iters] += ncg;
-      loc.cg_iters_total += ncg;
-      // backtracking on phi(lam) = rms(R(F + lam dF))^2 with sufficient decrease;
-      // after a rejected trial the next lam minimises the quadratic through
-      // phi(0), the Newton slope -2 phi(0) and phi(lam), kept in [0.1, 0.5] lam.
-      // A trial at which some voxel's local update fails (the step asks for
-      // slips above the local cap) is halved on a budget of its own: the
-      // current iterate itself has a converged local state, so a small enough
-      // step always passes.
-      lam = 1.0;
-      const double f0 = rabs * rabs;
-      int shrink = 0, local_cuts = 0;
-      while (shrink <= h->opt.max_halvings && local_cuts <= 40) {
-        st = eval_residual(h, dt, lam, 1 - cur, cur, mask, Pb, &rt, &sct, &lm, &lf);
-        if (st != RVE_OK) return finish(st);
-        if (lf == 0 && rt < rabs * (1.0 - 1e-4 * lam)) { acc = true; break; }
-        double next = 0.5 * lam;
-        if (lf == 0 && std::isfinite(rt)) {
-          const double c = (rt * rt - f0 * (1.0 - 2.0 * lam)) / (lam * lam);
-          if (c > 0.0) next = std::fmin(std::fmax(f0 / c, 0.1 * lam), 0.5 * lam);
-          ++shrink;
-        } else {
-          ++local_cuts;
-        }
-        lam = next;
-        ++loc.halvings;
+      if (e != cudaSuccess) {
+        h->err = cudaGetErrorString(e);
+        return finish(RVE_ECUDA);
       }
+      st = newton_solve(h, dt, mask, Ps, k == 1 ? -1 : h->cur, loc, h->opt.max_newton);
     }
-    if (!acc) {
-      if (lf) return finish(fail(h, RVE_ENOCONV_LOCAL, "local update did not converge in the line search"));
-      if (!cgok) return finish(fail(h, RVE_ENOCONV_CG, "the Krylov solve did not converge"));
-      return finish(fail(h, RVE_ENOCONV_NEWTON, "no step along the Newton direction lowers the residual"));
-    }
-    if (cudaError_t e = launch_axpy_F(h, lam, h->stream)) {
-      h->err = cudaGetErrorString(e);
-      return finish(RVE_ECUDA);
-    }
-    cur = 1 - cur;
-    h->cur = cur;
-    rabs = rt;
-    res = rt / sct;
-    loc.local_max_iters = lm > loc.local_max_iters ? lm : loc.local_max_iters;
-    ++loc.newton_iters;
-    if (loc.newton_iters <= RVE_MAX_NEWTON_LOG) loc.residuals[loc.newton_iters] = res;
   }
+  if (st != RVE_OK) return finish(st);
   if (h->sens_on) {
     h->sens_valid = 0;
     st = sens_update(h, mask, dt);
@@ -1200,6 +1257,22 @@ rve_status rve_eval_hardening(rve_t* h) {
   if (!h) return RVE_EINVAL;
   RVE_TRY(build_stale_tangent(h));   // before the frozen hardening state changes
   RVE_TRY(run_hardening(h));
+  RVE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return RVE_OK;
+}
+
+rve_status rve_eval_nye(rve_t* h, int scheme) {
+  if (!h || (scheme != 0 && scheme != 1)) return RVE_EINVAL;
+  if (scheme == 0) {
+    RVE_TRY(run_curl(h, h->Fp, h->nye));
+  } else {
+    SpecParams sp = project_params(h, (const uint8_t*)"\0\0\0\0\0\0\0\0\0", nullptr, nullptr);
+    sp.op = OP_CURL_STD;
+    h->fft_cat = RVE_K_FFT_CURL;
+    const rve_status st = run_project(h, h->Fp, h->nye, sp);
+    h->fft_cat = -1;
+    RVE_TRY(st);
+  }
   RVE_CUDA(h, cudaStreamSynchronize(h->stream));
   return RVE_OK;
 }

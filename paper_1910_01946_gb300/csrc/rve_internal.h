@@ -25,7 +25,9 @@ struct FFTPlan {
 //   OP_CURL:    9 fields, G_ij = -eps_jkl D_k X_il
 //   OP_LAPINV:  3 fields, each multiplied by 1 / (64 nvox sum_m s2_m prod_{j!=m} c2_j),
 //               the inverse of D^H D for the unscaled rotated-scheme stencils (0 where it vanishes)
-enum SpecOp { OP_PROJECT = 0, OP_CURL = 1, OP_LAPINV = 2 };
+//   OP_CURL_STD: 9 fields, G_ij = -eps_jkl D_k X_il with the standard (continuous)
+//               spectral derivative D_k = i xi_k / h (Nyquist: 0), for comparison
+enum SpecOp { OP_PROJECT = 0, OP_CURL = 1, OP_LAPINV = 2, OP_CURL_STD = 3 };
 
 struct SpecParams {
   int op;
@@ -45,6 +47,7 @@ struct AxisTables {
   const double* s2;     // sin^2(xi_k / 2)
   const double* c2;     // cos^2(xi_k / 2)
   const float2* tw32;   // the twiddles rounded to float (mixed precision)
+  const double* xi;     // xi_k = 2 pi k' / n (signed k'), 0 at Nyquist: the standard frequency
 };
 
 // Unit direction in the material parameters (tau0, K, alpha, b) of one
@@ -254,6 +257,8 @@ cudaError_t launch_lincomb(const rve_s* h, double* out, double c0, const double*
 cudaError_t launch_axpy_F(const rve_s* h, double lambda, cudaStream_t s);
 cudaError_t launch_predictor(const rve_s* h, const double* dFb, const double* dFb_prev, double ratio,
                              int extrapolate, cudaStream_t s);
+// F += shift on every voxel (components as given)
+cudaError_t launch_shift_F(const rve_s* h, const double* shift, cudaStream_t s);
 cudaError_t launch_commit(const rve_s* h, cudaStream_t s);
 cudaError_t launch_macro(const rve_s* h, cudaStream_t s);
 cudaError_t launch_output_field(const rve_s* h, int which, const double* P, const double* S, double* dst,

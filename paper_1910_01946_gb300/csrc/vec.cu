@@ -401,7 +401,7 @@ __global__ void k_axpy(size_t n, double* __restrict__ y, const double* __restric
 
 struct Nine { double v[9]; };
 
-__global__ void k_predictor(size_t nvox, double* __restrict__ F, const double* __restrict__ Fc,
+__global__ void k_predictor(size_t nvox, double* F, const double* Fc,
                             const double* __restrict__ dFl, Nine shift, double ratio, int extrapolate) {
   for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (size_t)gridDim.x * blockDim.x) {
 #pragma unroll
@@ -608,6 +608,16 @@ cudaError_t launch_predictor(const rve_s* h, const double* dFb, const double* dF
   {
     ProfScope ps_(h, RVE_K_OTHER, s);
     k_predictor<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, h->F, h->F_c, h->dF_last, sh, ratio, extrapolate);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shift_F(const rve_s* h, const double* shift, cudaStream_t s) {
+  Nine sh;
+  for (int k = 0; k < 9; ++k) sh.v[k] = shift[k];
+  {
+    ProfScope ps_(h, RVE_K_OTHER, s);
+    k_predictor<<<RVE_RED_BLOCKS, RVE_RED_THREADS, 0, s>>>(h->nvox, h->F, h->F, h->dF_last, sh, 0.0, 0);
   }
   return cudaGetLastError();
 }

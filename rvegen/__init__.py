@@ -190,3 +190,16 @@ def sweep_workloads():
         out.append(Workload(f"sweep{j:02d}_{n}_{g}g_{('Cu', 'Al', 'Ag', 'Ni')[j % 4]}", n, g,
                             ("Cu", "Al", "Ag", "Ni")[j % 4], 0.02, 20, seed=1300 + j, L=100e-6))
     return out
+
+
+def bicrystal_slip_jump(n: int, gamma: float = 1e-3) -> np.ndarray:
+    """A plastic distortion that jumps across grain boundaries (the input of
+    the Gibbs comparison of the Nye tensor): two slabs along x, x < n/2 with
+    the single slip Fp = I + gamma s (x) m on the system s = [-1 0 1]/sqrt 2,
+    m = (1 1 1)/sqrt 3, and x >= n/2 with Fp = I.  Numpy shape
+    (n, n, n, 3, 3) = (z, y, x, i, j)."""
+    s = np.array([-1.0, 0.0, 1.0]) / math.sqrt(2.0)
+    m = np.array([1.0, 1.0, 1.0]) / math.sqrt(3.0)
+    Fp = np.tile(np.eye(3), (n, n, n, 1, 1)).astype(np.float64)
+    Fp[:, :, : n // 2] += gamma * np.outer(s, m)
+    return Fp

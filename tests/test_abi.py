@@ -44,9 +44,35 @@ def test_workspace_bytes_validation(lib):
     assert 7.5 * small < big < 8.5 * small
 
 
-def test_struct_layouts_match_header():
+def test_struct_layouts_match_header(tmp_path):
+    """Every field offset and the size of each struct shared with the binding,
+    as the C compiler lays them out from include/rve.h, equal the ctypes
+    layout the binding uses."""
     import ctypes as C
+    import shutil
+    import subprocess
     import paper_1910_01946_gb300 as pkg
-    assert C.sizeof(pkg.rve_options) == 4 * 8 + 11 * 4 + 4   # eleven int32 fields and tail padding
-    assert C.sizeof(pkg.rve_material) == 7 * 8 + 6 * 8 + 8 + 5 * 8 + 8
-    assert pkg.rve_step_info.local_iters_total.offset == 32 and pkg.rve_step_info.residual.offset == 48
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"rve_options": pkg.rve_options, "rve_material": pkg.rve_material, "rve_step_info": pkg.rve_step_info}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rve.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            name, field, val = ln.split()
+            got[(name, field)] = int(val)
+    for name, cls in structs.items():
+        assert got[(name, "sizeof")] == C.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)

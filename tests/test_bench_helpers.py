@@ -40,3 +40,17 @@ def test_traffic_table_names_known_categories():
     cats = set(b.kernel_models(64, 64, 64, local=(1, 1, 1)))
     for (cat, prec), v in b.TRAFFIC_64.items():
         assert cat in cats and prec in (0, 1) and v > 0
+
+
+def test_hall_petch_fit_recovers_known_law():
+    # sigma_y = sigma_inf (1 + C (D sqrt(rho))^-x) at four grain sizes
+    b = bench()
+    import numpy as np
+    rho, C, x = 1.0e12, 3.7, 0.66
+    d = np.array([62e-6, 40e-6, 27e-6, 17e-6])
+    s_inf = np.array([80.0, 81.0, 79.5, 80.4])
+    s_y = s_inf * (1 + C * (d * np.sqrt(rho)) ** -x)
+    Cf, xf = b.hall_petch_fit(d, s_y, s_inf, rho)
+    assert abs(Cf / C - 1) < 1e-12 and abs(xf - x) < 1e-12
+    # no strengthening at some size: nothing to fit
+    assert b.hall_petch_fit(d, s_inf, s_inf, rho) is None

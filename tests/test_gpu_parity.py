@@ -353,3 +353,56 @@ def test_staged_tangent_apply_matches_plain_loads(pkg):
     for name, base in (("F", EYE9), ("P", None), ("FP", EYE9), ("RHO_GND", None)):
         assert comp_err(a.field(name), b.field(name), base) < 1e-9, name
     a.close(); b.close()
+
+
+def test_nye_schemes_match_oracle_and_show_gibbs_ringing(pkg):
+    """rve_eval_nye on a bicrystal whose Fp jumps across the slab boundaries
+    (App. B): the rotated scheme against the oracle's stencil (exactly local
+    to the boundary layers), the standard spectral derivative against the
+    oracle's FFT form (Gibbs oscillations through the grains)."""
+    n = 32
+    Fp = rvegen.bicrystal_slip_jump(n)
+    gid = np.zeros((n, n, n), dtype=np.int32)
+    g = pkg.RVE(gid, np.array([[1.0, 0, 0, 0]]), rvegen.material("Cu"), 20e-6)
+    g.set_field("FP", Fp.reshape(gid.shape + (9,)))
+    h = 20e-6 / n
+    g.eval_nye(0)
+    Gr = g.field("NYE")
+    g.eval_nye(1)
+    Gs = g.field("NYE")
+    ref_r = sp.nye_tensor(Fp, h).reshape(gid.shape + (9,))
+    ref_s = sp.nye_tensor_standard(Fp, h).reshape(gid.shape + (9,))
+    assert relerr(Gr, ref_r) < 1e-12
+    assert relerr(Gs, ref_s) < 1e-12
+    col_r = np.abs(Gr).max(axis=(0, 1, 3))
+    col_s = np.abs(Gs).max(axis=(0, 1, 3))
+    assert np.abs(col_r[[x for x in range(n) if x not in (n // 2 - 1, n - 1)]]).max() < 1e-12 * col_r.max()
+    assert col_s[[n // 4, 3 * n // 4]].min() > 0.1 * col_s.max()
+    with pytest.raises(pkg.RVEError):
+        g.eval_nye(2)
+    g.close()
+
+
+def test_load_continuation_reaches_the_same_increment(pkg):
+    """A direct Newton solve held to 6 iterations fails at the plastic onset
+    (it needs 16); the load continuation solves the same increment in stages
+    (8, each within 6 iterations).  The
+    converged increment equals the one a direct solve reaches (and the
+    oracle's)."""
+    wl = rvegen.Workload("cu8", 8, 5, "Cu", 0.004, 4, seed=31)
+    gid, quat, mat = wl.inputs()
+    a = pkg.RVE(gid, quat, mat, wl.edge, max_newton=6, continuation=6)
+    b = pkg.RVE(gid, quat, mat, wl.edge, continuation=0)
+    o = solver.RVE(gid, quat, mat, wl.edge)
+    staged = 0
+    for k in range(2):
+        ia = a.step(wl.dFbar(), MASK, np.zeros(9), wl.dt)
+        ib = b.step(wl.dFbar(), MASK, np.zeros(9), wl.dt)
+        assert o.step(wl.dFbar(), MASK, np.zeros(9), wl.dt).converged
+        assert ia["converged"] and ib["converged"] and ib["load_stages"] == 1
+        staged = max(staged, ia["load_stages"])
+    assert staged > 1
+    for name, base in (("F", EYE9), ("P", None), ("FP", EYE9), ("RHO_SSD", None)):
+        assert comp_err(a.field(name), b.field(name), base) < 1e-9, name
+    check_increment_fields(a, o)
+    a.close(); b.close()

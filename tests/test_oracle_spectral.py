@@ -5,6 +5,8 @@ defining properties of an orthogonal projection onto compatible fields."""
 import itertools
 
 import numpy as np
+
+import rvegen
 import pytest
 
 from oracle import crystal as cr
@@ -194,3 +196,71 @@ def test_nyquist_modes_with_two_components_are_zeroed():
     GX = sp.project(X, UNIAXIAL, h)
     assert np.allclose(GX[..., 0, 0], np.cos(np.pi * x), atol=1e-14)
     assert np.abs(GX[..., 0, 1]).max() < 1e-14
+
+
+# ---- standard spectral derivative (App. A's continuous frequencies) and the
+# Gibbs oscillations it produces at a grain boundary (App. B)
+
+def _band_limited_fp(n, h, seed):
+    """Fp = I + sum of three plane waves with |k| below Nyquist on every axis,
+    and its exact derivatives d_k Fp_il (analytic)."""
+    rng = np.random.default_rng(seed)
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    Fp = np.tile(np.eye(3), (n, n, n, 1, 1)).astype(float)
+    dFp = np.zeros((n, n, n, 3, 3, 3))
+    for _ in range(3):
+        kv = rng.integers(-(n // 2 - 1), n // 2, size=3)
+        a = 1e-3 * rng.standard_normal((3, 3))
+        ph = 2 * np.pi * (kv[0] * x + kv[1] * y + kv[2] * z) / n + rng.random()
+        Fp += a * np.sin(ph)[..., None, None]
+        for k in range(3):
+            dFp[..., k] += a * (2 * np.pi * kv[k] / (n * h) * np.cos(ph))[..., None, None]
+    return Fp, dFp
+
+
+def test_standard_curl_is_exact_on_band_limited_fields():
+    n, h = 12, 0.7
+    Fp, dFp = _band_limited_fp(n, h, 5)
+    G = sp.nye_tensor_standard(Fp, h)
+    exact = -np.einsum("jkl,...ilk->...ij", sp.LEVI, dFp)
+    assert np.abs(exact).max() > 1e-3
+    assert np.abs(G - exact).max() < 1e-12 * np.abs(exact).max()
+
+
+def test_standard_curl_of_a_band_limited_gradient_vanishes():
+    n, h = 10, 1.3
+    rng = np.random.default_rng(9)
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    grad = np.zeros((n, n, n, 3, 3))
+    for _ in range(4):
+        kv = rng.integers(-(n // 2 - 1), n // 2, size=3)
+        c = rng.standard_normal(3)
+        ph = 2 * np.pi * (kv[0] * x + kv[1] * y + kv[2] * z) / n
+        for j in range(3):           # (grad u)_ij = d_j u_i, u_i = c_i sin(ph)
+            grad[..., :, j] += c * (2 * np.pi * kv[j] / (n * h) * np.cos(ph))[..., None]
+    G = sp.nye_tensor_standard(np.eye(3) + grad, h)
+    assert np.abs(grad).max() > 0.1
+    assert np.abs(G).max() < 1e-12 * np.abs(grad).max()
+
+
+def test_rotated_nye_is_local_and_standard_rings_at_a_slip_jump():
+    # App. B: at a jump of Fp the rotated stencil gives a Nye tensor confined to
+    # the voxel layers at the boundary; the standard derivative gives Gibbs
+    # oscillations that reach into the grains with alternating sign
+    n, h = 32, 1.0
+    Fp = rvegen.bicrystal_slip_jump(n)
+    Gr = np.abs(sp.nye_tensor(Fp, h)).max(axis=(0, 1, 3, 4))      # per x column
+    Gs_full = sp.nye_tensor_standard(Fp, h)
+    Gs = np.abs(Gs_full).max(axis=(0, 1, 3, 4))
+    # the rotated Nye tensor lives on the voxel corners n + 1/2: the jumps
+    # between x = 15 | 16 and 31 | 0 land on the layers 15 and 31 alone
+    near = [n // 2 - 1, n - 1]
+    others = [x for x in range(n) if x not in near]
+    assert Gr[near].min() > 1e-5
+    assert Gr[others].max() == 0.0                                # exactly local
+    centres = [n // 4, 3 * n // 4]
+    assert Gs[centres].min() > 0.1 * Gs.max()                     # the ringing reaches the grain centres
+    # sign alternation from voxel to voxel along x inside the grains (checkerboard)
+    i, j = np.unravel_index(np.abs(Gs_full[0, 0]).max(axis=0).argmax(), (3, 3))
+    for grain in (Gs_full[0, 0, : n // 2, i, j], Gs_full[0, 0, n // 2:, i, j]):
+        assert np.all(np.sign(grain[1:]) != np.sign(grain[:-1]))
