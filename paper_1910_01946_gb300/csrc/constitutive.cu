@@ -184,10 +184,17 @@ __device__ void lu6(double* J, int* piv) {
       if (v > best) { best = v; p = i; }
     }
     piv[k] = p;
-    if (p != k) {
+    // the swap of rows k and p as selects over the candidate rows: every index
+    // is a compile-time constant, so J stays in registers (a runtime row
+    // index would place the whole matrix in local memory)
+#pragma unroll
+    for (int i = k + 1; i < 6; ++i) {
+      const bool sw = p == i;
 #pragma unroll
       for (int j = 0; j < 6; ++j) {
-        const double t = J[6 * k + j]; J[6 * k + j] = J[6 * p + j]; J[6 * p + j] = t;
+        const double a = J[6 * k + j], b = J[6 * i + j];
+        J[6 * k + j] = sw ? b : a;
+        J[6 * i + j] = sw ? a : b;
       }
     }
     const double inv = 1.0 / J[6 * k + k];
@@ -206,7 +213,13 @@ __device__ void lu6_solve(const double* LU, const int* piv, double* b) {
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     const int p = piv[k];
-    if (p != k) { const double t = b[k]; b[k] = b[p]; b[p] = t; }
+#pragma unroll
+    for (int i = k + 1; i < 6; ++i) {      // swap b[k], b[p] by selects (registers only)
+      const bool sw = p == i;
+      const double x = b[k], y = b[i];
+      b[k] = sw ? y : x;
+      b[i] = sw ? x : y;
+    }
   }
 #pragma unroll
   for (int i = 1; i < 6; ++i)
