@@ -271,10 +271,11 @@ enum {
 rve_status rve_profile(rve_t* rve, int enable);
 /* The launch shapes in use (no counterpart in the paper): out[0] grid cap of
  * the divergence stencil (blocks),
- * out[1] block count the FFT tile rules aim for, out[2] 1 if the FP32 tangent
- * apply is staged by bulk copies, out[3] 1 if the autotuner chose them
- * (host array of 4). */
-rve_status rve_get_tuning(rve_t* rve, int32_t out[4]);
+ * out[1] block count the FFT tile rules aim for in the x passes, out[2] 1 if
+ * the FP32 tangent apply is staged by bulk copies, out[3] 1 if the autotuner
+ * chose them, out[4] and out[5] the FFT block counts aimed for in the y
+ * passes and the z pass (host array of 6). */
+rve_status rve_get_tuning(rve_t* rve, int32_t out[6]);
 rve_status rve_kernel_stats(rve_t* rve, int64_t* launches, double* ms);
 
 /* Device time of the hand-written FFT alone (no counterpart in the paper:

@@ -365,10 +365,12 @@ class RVE:
         return ms.value
 
     def tuning(self):
-        """Launch shapes in use: divergence grid cap, FFT fill target, staged FP32 apply, autotuned."""
-        out = np.zeros(4, dtype=np.int32)
+        """Launch shapes in use: divergence grid cap, FFT fill targets (x, y, z passes), staged FP32
+        apply, autotuned."""
+        out = np.zeros(6, dtype=np.int32)
         self._check(load_library().rve_get_tuning(self.h, _ptr(out)), "rve_get_tuning")
-        return dict(div_blocks=int(out[0]), fft_fill=int(out[1]), tma=bool(out[2]), autotuned=bool(out[3]))
+        return dict(div_blocks=int(out[0]), fft_fill=int(out[1]), tma=bool(out[2]), autotuned=bool(out[3]),
+                    fft_fill_y=int(out[4]), fft_fill_z=int(out[5]))
 
     def stress_sensitivity(self):
         """d<P>/d theta of the last increment, shape (4, 3, 3), theta = PARAMS."""

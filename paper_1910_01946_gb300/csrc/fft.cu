@@ -455,7 +455,7 @@ cudaError_t fwd(const rve_s* h, const R* in, cudaStream_t s, const double* done,
     k_fft_x_r2c<R><<<gx, threads_for(rpb * h->n0), shx, s>>>(in, spect<R>(h), h->n0, h->n1, h->n2, h->nkx, rpb,
                                                              to_dev(h->plan[0]), twt<R>(h, 0), done);
   }
-  const int ty = tile_y(h->n1, h->n2, h->nkx, nf, h->fft_fill);
+  const int ty = tile_y(h->n1, h->n2, h->nkx, nf, h->fft_fill_y);
   dim3 gy((h->nkx + ty - 1) / ty, h->n2, nf);
   size_t shy = 2 * (size_t)ty * h->n1 * sizeof(CX<R>);
   {
@@ -468,7 +468,7 @@ cudaError_t fwd(const rve_s* h, const R* in, cudaStream_t s, const double* done,
 
 template <typename R>
 cudaError_t zop(const rve_s* h, const SpecParams& sp, cudaStream_t s, const double* done, int nf) {
-  const int tz = tile_z(h->n1, h->n2, h->nkx, nf, h->fft_fill);
+  const int tz = tile_z(h->n1, h->n2, h->nkx, nf, h->fft_fill_z);
   dim3 g((h->nkx + tz - 1) / tz, h->n1, nf / 3);
   size_t sh = 2 * 3 * (size_t)tz * h->n2 * sizeof(CX<R>);
   const int zthreads = threads_for(3 * tz * h->n2);
@@ -482,7 +482,7 @@ cudaError_t zop(const rve_s* h, const SpecParams& sp, cudaStream_t s, const doub
 
 template <typename R>
 cudaError_t inv(const rve_s* h, R* out, cudaStream_t s, const double* done, int nf) {
-  const int ty = tile_y(h->n1, h->n2, h->nkx, nf, h->fft_fill);
+  const int ty = tile_y(h->n1, h->n2, h->nkx, nf, h->fft_fill_y);
   dim3 gy((h->nkx + ty - 1) / ty, h->n2, nf);
   size_t shy = 2 * (size_t)ty * h->n1 * sizeof(CX<R>);
   {

@@ -130,7 +130,9 @@ struct rve_s {
   int num_sms = 152;        // of the handle's device
   // launch shapes (rve_options.autotune times candidates at create):
   int div_blocks = 4 * 152; // grid cap of the divergence stencil
-  int fft_fill = 4 * 152;   // block count the FFT tile rules aim for
+  int fft_fill = 4 * 152;   // block count the FFT tile rules aim for: x passes
+  int fft_fill_y = 8 * 152; // y passes
+  int fft_fill_z = 4 * 152; // z pass
   bool autotuned = false;
   bool tma_apply = false;   // FP32 tangent apply staged by bulk copies (rve_options.tma)
   int fft_cat = -1;         // >= 0: the FFT passes are counted in this category (the Nye curl)
