@@ -8,7 +8,7 @@
 //
 // Layout.  Real fields: [c][z][y][x] (x fastest).  Half spectrum:
 // [c][z][y][kx], kx = 0..n0/2.  Passes (each a kernel, each transform staged
-// in shared memory and done by a mixed-radix 4/2/3 Stockham autosort):
+// in shared memory and done by a mixed-radix 8/4/2/3 Stockham autosort):
 //   X  (R2C): two real rows y, y+1 packed as one complex row, one length-n0
 //             FFT, then the two half spectra are separated;
 //   Y  (C2C): tiles of consecutive kx columns, length-n1 FFTs;
@@ -76,7 +76,43 @@ __device__ void stockham_pass(const CX<RT>* __restrict__ src, CX<RT>* __restrict
     const cplx* X = src + tr * N;
     cplx* Y = dst + tr * N;
     const int d = (j / Ns) * Ns * R + k;
-    if (R == 4) {
+    if (R == 8) {
+      // radix 8 as a radix-2 step (a_m +/- a_{m+4}), the factors W8^m on the
+      // differences, then two radix-4 DFTs (even and odd outputs)
+      cplx a[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) a[m] = X[j + m * nb];
+      if (k) {
+#pragma unroll
+        for (int m = 1; m < 8; ++m) a[m] = twiddle<SIGN, RT>(a[m], tw, m * k * twstep);
+      }
+      const RT r2 = (RT)0.70710678118654752440;    // 1/sqrt(2)
+      cplx b[4], c[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) { b[m] = add(a[m], a[m + 4]); c[m] = sub(a[m], a[m + 4]); }
+      // c1 *= W8^(sign), c2 *= -/+ i, c3 *= W8^(3 sign)
+      {
+        const cplx c1 = c[1], c3 = c[3];
+        if (SIGN < 0) {
+          c[1] = mk<RT>(r2 * (c1.x + c1.y), r2 * (c1.y - c1.x));
+          c[3] = mk<RT>(r2 * (c3.y - c3.x), -r2 * (c3.x + c3.y));
+        } else {
+          c[1] = mk<RT>(r2 * (c1.x - c1.y), r2 * (c1.x + c1.y));
+          c[3] = mk<RT>(-r2 * (c3.x + c3.y), r2 * (c3.x - c3.y));
+        }
+        c[2] = mul_i<SIGN, RT>(c[2]);
+      }
+      const cplx t0 = add(b[0], b[2]), t1 = sub(b[0], b[2]), t2 = add(b[1], b[3]), t3 = mul_i<SIGN, RT>(sub(b[1], b[3]));
+      const cplx u0 = add(c[0], c[2]), u1 = sub(c[0], c[2]), u2 = add(c[1], c[3]), u3 = mul_i<SIGN, RT>(sub(c[1], c[3]));
+      Y[d] = add(t0, t2);
+      Y[d + 4 * Ns] = sub(t0, t2);
+      Y[d + 2 * Ns] = add(t1, t3);
+      Y[d + 6 * Ns] = sub(t1, t3);
+      Y[d + Ns] = add(u0, u2);
+      Y[d + 5 * Ns] = sub(u0, u2);
+      Y[d + 3 * Ns] = add(u1, u3);
+      Y[d + 7 * Ns] = sub(u1, u3);
+    } else if (R == 4) {
       cplx a0 = X[j], a1 = X[j + nb], a2 = X[j + 2 * nb], a3 = X[j + 3 * nb];
       if (k) {
         a1 = twiddle<SIGN, RT>(a1, tw, k * twstep);
@@ -420,11 +456,15 @@ int tile_z(int n1, int n2, int nkx, int nf, int fill) {
   while (t > 1 && (long)((nkx + t - 1) / t) * n1 * (nf / 3) < fill && 3 * t * n2 > 256) t /= 2;
   return t;
 }
-// threads for a block holding `elems` complex values (radix-4 butterflies: elems / 4)
-int threads_for(int elems) {
-  int t = (elems / 4 + 31) / 32 * 32;
+// threads for a block holding `elems` complex values: one per `per` values
+// (the x and y passes: one butterfly of the plan's largest radix, its first
+// pass, per thread; the z pass, whose tiles are narrow and few per SM, keeps
+// one thread per four values for the warps that hide its latency)
+int threads_for(int elems, int per) {
+  int t = (elems / per + 31) / 32 * 32;
   return t < 64 ? 64 : (t > 256 ? 256 : t);
 }
+int first_radix(const FFTPlan& pl) { return pl.npass > 0 ? pl.radix[0] : 4; }
 
 OpTables op_tables(const rve_s* h) {
   OpTables T;
@@ -452,7 +492,7 @@ cudaError_t fwd(const rve_s* h, const R* in, cudaStream_t s, const double* done,
   size_t shx = 2 * (size_t)rpb * h->n0 * sizeof(CX<R>);
   {
     ProfScope ps_(h, h->fft_cat >= 0 ? h->fft_cat : RVE_K_FFT_X_R2C, s);
-    k_fft_x_r2c<R><<<gx, threads_for(rpb * h->n0), shx, s>>>(in, spect<R>(h), h->n0, h->n1, h->n2, h->nkx, rpb,
+    k_fft_x_r2c<R><<<gx, threads_for(rpb * h->n0, first_radix(h->plan[0])), shx, s>>>(in, spect<R>(h), h->n0, h->n1, h->n2, h->nkx, rpb,
                                                              to_dev(h->plan[0]), twt<R>(h, 0), done);
   }
   const int ty = tile_y(h->n1, h->n2, h->nkx, nf, h->fft_fill_y);
@@ -460,7 +500,7 @@ cudaError_t fwd(const rve_s* h, const R* in, cudaStream_t s, const double* done,
   size_t shy = 2 * (size_t)ty * h->n1 * sizeof(CX<R>);
   {
     ProfScope ps_(h, h->fft_cat >= 0 ? h->fft_cat : RVE_K_FFT_Y, s);
-    k_fft_y<-1, R><<<gy, threads_for(ty * h->n1), shy, s>>>(spect<R>(h), h->n1, h->n2, h->nkx, ty,
+    k_fft_y<-1, R><<<gy, threads_for(ty * h->n1, first_radix(h->plan[1])), shy, s>>>(spect<R>(h), h->n1, h->n2, h->nkx, ty,
                                                             to_dev(h->plan[1]), twt<R>(h, 1), done);
   }
   return cudaGetLastError();
@@ -471,7 +511,7 @@ cudaError_t zop(const rve_s* h, const SpecParams& sp, cudaStream_t s, const doub
   const int tz = tile_z(h->n1, h->n2, h->nkx, nf, h->fft_fill_z);
   dim3 g((h->nkx + tz - 1) / tz, h->n1, nf / 3);
   size_t sh = 2 * 3 * (size_t)tz * h->n2 * sizeof(CX<R>);
-  const int zthreads = threads_for(3 * tz * h->n2);
+  const int zthreads = threads_for(3 * tz * h->n2, 4);
   {
     ProfScope ps_(h, h->fft_cat >= 0 ? h->fft_cat : RVE_K_FFT_Z_OP, s);
     k_fft_z_op<R><<<g, zthreads, sh, s>>>(spect<R>(h), h->n1, h->n2, h->nkx, tz, to_dev(h->plan[2]), twt<R>(h, 2),
@@ -487,7 +527,7 @@ cudaError_t inv(const rve_s* h, R* out, cudaStream_t s, const double* done, int 
   size_t shy = 2 * (size_t)ty * h->n1 * sizeof(CX<R>);
   {
     ProfScope ps_(h, h->fft_cat >= 0 ? h->fft_cat : RVE_K_FFT_Y_INV, s);
-    k_fft_y<+1, R><<<gy, threads_for(ty * h->n1), shy, s>>>(spect<R>(h), h->n1, h->n2, h->nkx, ty,
+    k_fft_y<+1, R><<<gy, threads_for(ty * h->n1, first_radix(h->plan[1])), shy, s>>>(spect<R>(h), h->n1, h->n2, h->nkx, ty,
                                                             to_dev(h->plan[1]), twt<R>(h, 1), done);
   }
   const int rpb = rows_per_block(h->n0, h->n1, h->n2, nf, h->fft_fill);
@@ -495,7 +535,7 @@ cudaError_t inv(const rve_s* h, R* out, cudaStream_t s, const double* done, int 
   size_t shx = 2 * (size_t)rpb * h->n0 * sizeof(CX<R>);
   {
     ProfScope ps_(h, h->fft_cat >= 0 ? h->fft_cat : RVE_K_FFT_X_C2R, s);
-    k_fft_x_c2r<R><<<gx, threads_for(rpb * h->n0), shx, s>>>(spect<R>(h), out, h->n0, h->n1, h->n2, h->nkx, rpb,
+    k_fft_x_c2r<R><<<gx, threads_for(rpb * h->n0, first_radix(h->plan[0])), shx, s>>>(spect<R>(h), out, h->n0, h->n1, h->n2, h->nkx, rpb,
                                                              to_dev(h->plan[0]), twt<R>(h, 0), done);
   }
   return cudaGetLastError();
@@ -509,10 +549,11 @@ cudaError_t launch_lapinv_table(const rve_s* h, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-void make_plan(int n, FFTPlan* p) {
+void make_plan(int n, FFTPlan* p, int max_radix) {
   p->n = n;
   p->npass = 0;
   int m = n;
+  while (max_radix >= 8 && m % 8 == 0) { p->radix[p->npass++] = 8; m /= 8; }
   while (m % 4 == 0) { p->radix[p->npass++] = 4; m /= 4; }
   if (m % 2 == 0) { p->radix[p->npass++] = 2; m /= 2; }
   while (m % 3 == 0) { p->radix[p->npass++] = 3; m /= 3; }

@@ -82,7 +82,7 @@ extern "C" rve_status rve_project_noalloc(int n0, int n1, int n2, double L, cons
   h.stream = (cudaStream_t)cuda_stream;
   make_plan(n0, &h.plan[0]);
   make_plan(n1, &h.plan[1]);
-  make_plan(n2, &h.plan[2]);
+  make_plan(n2, &h.plan[2], 4);
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return RVE_ECUDA;

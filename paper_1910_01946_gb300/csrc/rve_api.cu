@@ -822,7 +822,7 @@ rve_status rve_create(const int32_t* grain_id, int n0, int n1, int n2, const dou
   for (int c = 0; c < 9; ++c) { h->dFbar_prev[c] = 0.0; h->Pmacro[c] = 0.0; h->Smacro[c] = 0.0; }
   make_plan(n0, &h->plan[0]);
   make_plan(n1, &h->plan[1]);
-  make_plan(n2, &h->plan[2]);
+  make_plan(n2, &h->plan[2], 4);
   Consts& c = h->cst;
   c.C11 = mat->C11; c.C12 = mat->C12; c.C44 = mat->C44; c.mu = h->mu; c.b = mat->b;
   c.tau0 = mat->tau0; c.alpha = mat->alpha; c.gdot0 = mat->gdot0; c.n = mat->n; c.K = mat->K; c.yc = mat->yc;

@@ -197,7 +197,10 @@ cudaError_t launch_fft_op(const rve_s* h, const SpecParams& sp, cudaStream_t s, 
                           int nf = 9);
 cudaError_t launch_fft_inverse(const rve_s* h, double* out, cudaStream_t s, const double* done = nullptr,
                                int nf = 9);
-void make_plan(int n, FFTPlan* p);
+// radix passes 8 (up to max_radix), 4, 2, 3.  The x and y passes take radix 8
+// (two shared-memory round trips for 64 points instead of three); the z pass,
+// whose narrow tiles leave few threads per block, is faster with radix 4
+void make_plan(int n, FFTPlan* p, int max_radix = 8);
 // fills h->lapw (once, at create)
 cudaError_t launch_lapinv_table(const rve_s* h, cudaStream_t s);
 cudaError_t launch_fft_forward32(const rve_s* h, const float* in, cudaStream_t s, const double* done);
