@@ -39,12 +39,12 @@ WORKLOAD = "cu64"
 FP64_PEAK_GFLOPS = 152 * 4 * 2.070   # 152 SMs x 2 DFMA (4 flop) per clock x 2.07 GHz = 1258.6
 # The oracle's own mix of work: conjugate-gradient iterations per local
 # evaluation (local update with tangent on every voxel).  Measured from whole
-# oracle increments, the full 20-increment history of the 16^3 / 8-grain Cu
-# workload on the GB300 machine's 16 host cores (bench.py --impl reference
-# --workload cu16 --full): 8957 CG iterations over 91 evaluations.  A timed
-# slice of the oracle keeps this mix, so that its voxel-iterations/s is the
-# one its whole increments reach.
-ORACLE_CG_PER_EVAL = 98.4
+# oracle increments of the 64^3 / 100-grain Cu workload itself: increments 2-5
+# (past the first increment's elastic-plastic transition, as the timed
+# increments are) took 5319 CG iterations over 30 evaluations (177, 186, 176
+# and 167 per evaluation).  A timed slice of the oracle keeps this mix, so that
+# its voxel-iterations/s is the one its whole increments reach.
+ORACLE_CG_PER_EVAL = 177.3
 
 
 def parse(argv=None):
