@@ -137,7 +137,6 @@ struct rve_s {
   bool tma_apply = false;   // FP32 tangent apply staged by bulk copies (rve_options.tma)
   int fft_cat = -1;         // >= 0: the FFT passes are counted in this category (the Nye curl)
   bool row_stencils = true; // row-strip stencils where the grid suits them (n0 = 32, 64, 96, 128)
-  int row_ly = 0;           // rows per strip of the row-strip stencils (0: from the occupancy)
   unsigned wait_polls = RVE_WAIT_POLLS_DEFAULT;   // its per-tile wait limit (rve_set_wait_limit)
   // forward-mode sensitivities (rve_sensitivity_enable): state tangents
   // dFp (9) and d rho_SSD (12) per parameter, double-buffered so that a

@@ -250,8 +250,9 @@ __global__ void __launch_bounds__(NT) k_grad_t(Grid3 g, Tiling T, const V* __res
 }
 
 // ---------------------------------------------------------------- row-strip stencils
-// For n0 = 32 NPL (NPL = 1..4) the stencils run one warp per strip of Ly
-// consecutive rows (x lines) of one z plane, a whole x line per warp with
+// For n0 = 32 NPL (NPL = 1..4) the stencils run one warp per run of
+// consecutive rows (x lines), walked as strips within z planes, a whole x
+// line per warp with
 // NPL adjacent points per lane (x = NPL lane + k), loaded as vectors.  The
 // stencil is applied separably, so every partial sum is formed once and
 // shared: z pairs (or differences), then y pairs of those, then the x step.
@@ -280,20 +281,52 @@ __device__ __forceinline__ void load_row(const V* __restrict__ src, V (&v)[NPL])
   }
 }
 
+// The rows (x lines) of the grid, n1 n2 of them in (z, y) order, split into
+// one contiguous run per warp of the grid, the runs differing in length by
+// at most one row: every SM gets the same work whatever the grid's shape.  A
+// run is walked as strips, each the part of the run inside one z plane; a
+// strip starts with a priming row (the partial sums of its row before or
+// after).  next() sets the next strip (z, ya .. yb - 1) and is false once
+// the run is done.
+struct RowRange {
+  unsigned r, e, n1;
+  int z, ya, yb;
+  __device__ bool next() {
+    if (r >= e) return false;
+    z = (int)(r / n1);
+    ya = (int)(r - (unsigned)z * n1);
+    const unsigned left = e - r, room = n1 - (unsigned)ya;
+    yb = ya + (int)(left < room ? left : room);
+    r += (unsigned)(yb - ya);
+    return true;
+  }
+};
+
+__device__ __forceinline__ RowRange row_range(const Grid3& g, int warps_per_block) {
+  const unsigned long long rows = (unsigned long long)g.n1 * g.n2;
+  const unsigned long long nw = (unsigned long long)gridDim.x * warps_per_block;
+  const unsigned long long w = (unsigned long long)blockIdx.x * warps_per_block + (threadIdx.x >> 5);
+  RowRange rr;
+  rr.r = (unsigned)(rows * w / nw);
+  rr.e = (unsigned)(rows * (w + 1) / nw);
+  rr.n1 = (unsigned)g.n1;
+  rr.z = rr.ya = rr.yb = 0;
+  return rr;
+}
+
 // Divergence d_i = sum_l D_l^T X_il (unscaled), as k_div.  Per voxel and row
 // i of X (fields A = X_i0, B = X_i1, C = X_i2): z pairs A = X(z) + X(z-1),
 // B likewise, C = X(z-1) - X(z); then with YS_A = A(y) + A(y-1),
 // YD_B = B(y-1) - B(y), YS_C = C(y) + C(y-1) and Q = YD_B + YS_C,
 //   d_i(x) = (Q - YS_A)(x) + (Q + YS_A)(x - 1).
 template <typename V, int NPL>
-__global__ void __launch_bounds__(32 * RW) k_div_rows(Grid3 g, int Ly, int nseg, const V* __restrict__ X,
+__global__ void __launch_bounds__(32 * RW) k_div_rows(Grid3 g, const V* __restrict__ X,
                                                      V* __restrict__ d, double* __restrict__ ds,
                                                      double* __restrict__ partial, unsigned int* __restrict__ ticket,
                                                      int check_done, unsigned mean_mask) {
   __shared__ double sh[320];
   if (check_done && ds[DS_DONE] != 0.0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int seg = blockIdx.x * RW + warp;
   const int left = (lane + 31) & 31;
   // the next row's loads are issued ahead of this row's arithmetic where the
   // registers allow it (up to three points per lane)
@@ -301,9 +334,9 @@ __global__ void __launch_bounds__(32 * RW) k_div_rows(Grid3 g, int Ly, int nseg,
   V mean[9];
 #pragma unroll
   for (int f = 0; f < 9; ++f) mean[f] = (V)0;
-  if (seg < g.n2 * nseg) {                              // warp-uniform
-    const int z = seg / nseg, sg = seg - z * nseg;
-    const int ya = sg * Ly, yb = min(ya + Ly, g.n1);
+  RowRange rr = row_range(g, RW);
+  while (rr.next()) {                                   // warp-uniform: one strip of one plane
+    const int z = rr.z, ya = rr.ya, yb = rr.yb;
     const unsigned plane = (unsigned)g.n0 * g.n1;
     const unsigned rz = (unsigned)z * plane, rzp = (unsigned)wrapi(z - 1, g.n2) * plane;
     V a[9][NPL], b[9][NPL];                             // loads of one row: plane z, plane z - 1
@@ -423,7 +456,7 @@ __global__ void __launch_bounds__(32 * RW) k_div_rows(Grid3 g, int Ly, int nseg,
 // YM = SM(y) + SM(y+1); q_i0 = YS(x+1) - YS(x), q_i1 = YD(x) + YD(x+1),
 // q_i2 = YM(x) + YM(x+1).  CG as in k_grad_t.
 template <bool CG, typename V, int NPL>
-__global__ void __launch_bounds__(32 * RW, NPL <= 2 ? 4 : 1) k_grad_rows(Grid3 g, int Ly, int nseg, const V* __restrict__ u,
+__global__ void __launch_bounds__(32 * RW, NPL <= 2 ? 4 : 1) k_grad_rows(Grid3 g, const V* __restrict__ u,
                                                       ZeroMode zm, double* __restrict__ Y, V* __restrict__ x,
                                                       V* __restrict__ r, const V* __restrict__ p,
                                                       double* __restrict__ ds, double* __restrict__ partial,
@@ -434,13 +467,12 @@ __global__ void __launch_bounds__(32 * RW, NPL <= 2 ? 4 : 1) k_grad_rows(Grid3 g
   V off[9];
 #pragma unroll
   for (int c = 0; c < 9; ++c) off[c] = zm.keep[c] ? (V)(ds[DS_XMEAN + c] + zm.add[c]) : (V)0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int seg = blockIdx.x * RW + warp;
+  const int lane = threadIdx.x & 31;
   const int right = (lane + 1) & 31;
   V acc = (V)0;
-  if (seg < g.n2 * nseg) {
-    const int z = seg / nseg, sg = seg - z * nseg;
-    const int ya = sg * Ly, yb = min(ya + Ly, g.n1);
+  RowRange rr = row_range(g, RW);
+  while (rr.next()) {                                   // warp-uniform: one strip of one plane
+    const int z = rr.z, ya = rr.ya, yb = rr.yb;
     const unsigned plane = (unsigned)g.n0 * g.n1;
     const unsigned rz = (unsigned)z * plane, rzn = (unsigned)wrapi(z + 1, g.n2) * plane;
     V a[3][NPL], c[3][NPL];                             // loads of one row: plane z, plane z + 1
@@ -551,29 +583,22 @@ __global__ void __launch_bounds__(32 * RW, NPL <= 2 ? 4 : 1) k_grad_rows(Grid3 g
 }
 
 struct RowShape {
-  int npl, Ly, nseg, nblocks;
+  int npl, nblocks;
 };
 
-// Rows per strip: every strip costs its rows plus one priming row (the z
-// pairs of the row before it), and the strips run in waves of (resident
-// blocks per SM x SMs x RW) warps, so Ly minimises waves x (Ly + 1).  With
-// h->div_blocks below its default (the autotuner's candidates) the strips
-// are made as many as that many blocks hold instead.
-RowShape row_shape_for(const rve_s* h, int blocks_per_sm) {
-  RowShape r{0, 0, 0, 0};
+// One wave of resident blocks: blocks_per_sm on every SM, at most `cap`
+// (the divergence passes h->div_blocks, which the autotuner varies), and no
+// more warps than rows.  The rows are split evenly over the warps (RowRange).
+RowShape row_shape_for(const rve_s* h, int blocks_per_sm, int cap) {
+  RowShape r{0, 0};
   if (h->n0 % 32 != 0 || h->n0 > 128) return r;
   r.npl = h->n0 / 32;
-  const long slots = (long)RW * h->num_sms * (blocks_per_sm > 0 ? blocks_per_sm : 1);
-  long best = -1, pick = 1;
-  for (int ly = 1; ly <= h->n1 && ly <= 16; ++ly) {
-    const long segs = (long)h->n2 * ((h->n1 + ly - 1) / ly);
-    const long cost = ((segs + slots - 1) / slots) * (ly + 1);
-    if (best < 0 || cost < best) { best = cost; pick = ly; }
-  }
-  if (h->row_ly > 0) pick = h->row_ly < h->n1 ? h->row_ly : h->n1;
-  r.Ly = (int)pick;
-  r.nseg = (h->n1 + r.Ly - 1) / r.Ly;
-  r.nblocks = (h->n2 * r.nseg + RW - 1) / RW;
+  const long rows = (long)h->n1 * h->n2;
+  long nb = (long)h->num_sms * (blocks_per_sm > 0 ? blocks_per_sm : 1);
+  if (cap > 0 && cap < nb) nb = cap;
+  if (nb > rows / RW) nb = rows / RW;
+  if (nb > 4096) nb = 4096;
+  r.nblocks = (int)(nb > 0 ? nb : 1);
   return r;
 }
 
@@ -588,9 +613,9 @@ template <typename V, int NPL>
 cudaError_t div_rows_n(const rve_s* h, const V* X, V* d, int check_done, unsigned mean_mask, cudaStream_t s,
                        const Grid3& g) {
   static const int bps = resident_blocks(k_div_rows<V, NPL>);
-  const RowShape rs = row_shape_for(h, bps);
-  k_div_rows<V, NPL><<<rs.nblocks, 32 * RW, 0, s>>>(g, rs.Ly, rs.nseg, X, d, h->dscal, h->partial,
-                                                    (unsigned int*)(h->dcount + 4), check_done, mean_mask);
+  const RowShape rs = row_shape_for(h, bps, h->div_blocks);
+  k_div_rows<V, NPL><<<rs.nblocks, 32 * RW, 0, s>>>(g, X, d, h->dscal, h->partial, (unsigned int*)(h->dcount + 4),
+                                                    check_done, mean_mask);
   return cudaGetLastError();
 }
 
@@ -609,8 +634,8 @@ template <bool CG, typename V, int NPL>
 cudaError_t grad_rows_n(const rve_s* h, const V* u, const ZeroMode& zm, double* Y, V* x, V* r, const V* p,
                         cudaStream_t s, const Grid3& g) {
   static const int bps = resident_blocks(k_grad_rows<CG, V, NPL>);
-  const RowShape rs = row_shape_for(h, bps);
-  k_grad_rows<CG, V, NPL><<<rs.nblocks, 32 * RW, 0, s>>>(g, rs.Ly, rs.nseg, u, zm, Y, x, r, p, h->dscal, h->partial,
+  const RowShape rs = row_shape_for(h, bps, 0);
+  k_grad_rows<CG, V, NPL><<<rs.nblocks, 32 * RW, 0, s>>>(g, u, zm, Y, x, r, p, h->dscal, h->partial,
                                                          (unsigned int*)(h->dcount + 4));
   return cudaGetLastError();
 }
