@@ -21,16 +21,51 @@ RVE_HD cplx cmul_i(cplx a, int sign) { return sign > 0 ? cmk(-a.y, a.x) : cmk(a.
 // <110> directions s' (|s'| = sqrt 2) per plane; the unit Schmid tensor is
 // s (x) m = s' m'^T / sqrt 6.  The order is the one the whole library (and its
 // field outputs) uses for slip-system indices 0..11.
-__device__ __constant__ const int8_t FCC_S[12][3] = {
-    {0, 1, -1}, {-1, 0, 1}, {1, -1, 0},
-    {0, 1, -1}, {1, 0, 1}, {1, 1, 0},
-    {0, 1, 1}, {1, 0, -1}, {1, 1, 0},
-    {0, 1, 1}, {1, 0, 1}, {1, -1, 0}};
-__device__ __constant__ const int8_t FCC_M[12][3] = {
-    {1, 1, 1}, {1, 1, 1}, {1, 1, 1},
-    {-1, 1, 1}, {-1, 1, 1}, {-1, 1, 1},
-    {1, -1, 1}, {1, -1, 1}, {1, -1, 1},
-    {1, 1, -1}, {1, 1, -1}, {1, 1, -1}};
+// As compile-time functions: the loops over systems are unrolled everywhere,
+// so every coefficient built from these is a constant there.
+__host__ __device__ constexpr int fcc_s(int a, int i) {
+  constexpr signed char t[12][3] = {
+      {0, 1, -1}, {-1, 0, 1}, {1, -1, 0},
+      {0, 1, -1}, {1, 0, 1}, {1, 1, 0},
+      {0, 1, 1}, {1, 0, -1}, {1, 1, 0},
+      {0, 1, 1}, {1, 0, 1}, {1, -1, 0}};
+  return t[a][i];
+}
+__host__ __device__ constexpr int fcc_m(int a, int i) {
+  constexpr signed char t[12][3] = {
+      {1, 1, 1}, {1, 1, 1}, {1, 1, 1},
+      {-1, 1, 1}, {-1, 1, 1}, {-1, 1, 1},
+      {1, -1, 1}, {1, -1, 1}, {1, -1, 1},
+      {1, 1, -1}, {1, 1, -1}, {1, 1, -1}};
+  return t[a][i];
+}
+
+// acc + c x for a small integer coefficient c that is a compile-time
+// constant (a product of slip-table entries): c = 0 adds nothing and c = +-1
+// is an addition or a subtraction, so no FP64 instruction is spent on the
+// table's zeros and ones.  (The compiler may not drop a product with 0.0 on
+// its own: for an infinite or NaN x it is not zero.)  `first` marks an empty
+// accumulator, whose first term is taken exactly.
+__device__ __forceinline__ double cacc(double acc, bool& first, int c, double x) {
+  if (c == 0) return acc;
+  double r;
+  if (first) r = c == 1 ? x : (c == -1 ? -x : (double)c * x);
+  else r = c == 1 ? acc + x : (c == -1 ? acc - x : fma((double)c, x, acc));
+  first = false;
+  return r;
+}
+
+// M += g s^a (x) m^a / sqrt 6 (the unit Schmid tensor of system a)
+__device__ __forceinline__ void add_schmid(double* M, int a, double g) {
+  const double gs = g * 0.40824829046386301637;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      bool f = false;
+      M[3 * i + j] = cacc(M[3 * i + j], f, fcc_s(a, i) * fcc_m(a, j), gs);
+    }
+}
 
 // Voigt order of a symmetric tensor: 11, 22, 33, 23, 13, 12
 #define V_I(a) ((a) < 3 ? (a) : ((a) == 3 ? 1 : 0))

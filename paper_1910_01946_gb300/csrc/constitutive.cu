@@ -41,30 +41,40 @@ __device__ __forceinline__ double ipow(double x, int n) {
   return r;
 }
 
+// |x|^n and |x|^(n-1) of the flow rule: the exponent n = 20 of the materials
+// here (rate sensitivity m = 1/n = 0.05) in five and six multiplications,
+// the same products in the same order as ipow's (bit-identical)
+__device__ __forceinline__ double pow_n(const Consts& c, double x) {
+  if (c.n_int == 20) {
+    const double x2 = x * x, x4 = x2 * x2, x8 = x4 * x4, x16 = x8 * x8;
+    return x4 * x16;
+  }
+  return c.n_int ? ipow(x, c.n_int) : pow(x, c.n);
+}
+__device__ __forceinline__ double pow_n1(const Consts& c, double x) {
+  if (c.n_int == 20) {
+    const double x2 = x * x, x3 = x * x2, x4 = x2 * x2, x8 = x4 * x4, x16 = x8 * x8;
+    return x3 * x16;
+  }
+  return c.n_int ? ipow(x, c.n_int - 1) : pow(x, c.n - 1.0);
+}
+
+// Coefficients of tau^a = S : s^a (x) m^a (times sqrt 6) on the Voigt
+// components (11, 22, 33, 23, 13, 12) of a symmetric S
+__host__ __device__ constexpr int tau_coef(int a, int k) {
+  return k < 3 ? fcc_s(a, k) * fcc_m(a, k)
+               : (k == 3 ? fcc_s(a, 1) * fcc_m(a, 2) + fcc_s(a, 2) * fcc_m(a, 1)
+                         : (k == 4 ? fcc_s(a, 0) * fcc_m(a, 2) + fcc_s(a, 2) * fcc_m(a, 0)
+                                   : fcc_s(a, 0) * fcc_m(a, 1) + fcc_s(a, 1) * fcc_m(a, 0)));
+}
+
 // tau^a = S : s^a (x) m^a for symmetric S in Voigt order (11,22,33,23,13,12)
 __device__ __forceinline__ double resolved(const double* S, int a) {
-  const double s0 = FCC_S[a][0], s1 = FCC_S[a][1], s2 = FCC_S[a][2];
-  const double m0 = FCC_M[a][0], m1 = FCC_M[a][1], m2 = FCC_M[a][2];
-  double t = s0 * m0 * S[0] + s1 * m1 * S[1] + s2 * m2 * S[2] + (s1 * m2 + s2 * m1) * S[3] +
-             (s0 * m2 + s2 * m0) * S[4] + (s0 * m1 + s1 * m0) * S[5];
+  bool first = true;
+  double t = 0.0;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) t = cacc(t, first, tau_coef(a, k), S[k]);
   return t * INV_SQRT6;
-}
-
-// d tau^a / d S_voigt
-__device__ __forceinline__ void tau_grad(int a, double* w) {
-  const double s0 = FCC_S[a][0], s1 = FCC_S[a][1], s2 = FCC_S[a][2];
-  const double m0 = FCC_M[a][0], m1 = FCC_M[a][1], m2 = FCC_M[a][2];
-  w[0] = s0 * m0 * INV_SQRT6; w[1] = s1 * m1 * INV_SQRT6; w[2] = s2 * m2 * INV_SQRT6;
-  w[3] = (s1 * m2 + s2 * m1) * INV_SQRT6; w[4] = (s0 * m2 + s2 * m0) * INV_SQRT6; w[5] = (s0 * m1 + s1 * m0) * INV_SQRT6;
-}
-
-// M += g * s^a (x) m^a
-__device__ __forceinline__ void add_schmid(double* M, int a, double g) {
-  const double gs = g * INV_SQRT6;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) M[3 * i + j] = fma(gs, (double)(FCC_S[a][i] * FCC_M[a][j]), M[3 * i + j]);
 }
 
 // cubic stiffness applied to a symmetric strain given by its tensor components
@@ -104,7 +114,7 @@ __device__ void evaluate(const Consts& c, const double* S, const double* A, cons
     const double t = resolved(S, a);
     const double x = t * tinv[a];
     const double ax = fabs(x);
-    const double xn = c.n_int ? ipow(ax, c.n_int) : pow(ax, c.n);
+    const double xn = pow_n(c, ax);
     double g = dt * c.gdot0 * xn;
     bad |= !(g <= c.dgam_max);
     g = copysign(g, x);
@@ -147,27 +157,32 @@ __device__ void jacobian(const Consts& c, const Eval& e, const double* tinv, dou
 #pragma unroll
   for (int a = 0; a < 12; ++a) {
     const double x = fabs(e.tau[a] * tinv[a]);
-    const double xn1 = c.n_int ? ipow(x, c.n_int - 1) : pow(x, c.n - 1.0);
+    const double xn1 = pow_n1(c, x);
     const double gp = dt * c.gdot0 * c.n * xn1 * tinv[a];
     dgp[a] = gp;
     // u = Ce s', w = Minv^T m'  (times 1/sqrt6 folded in below)
     double u[3], w[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      u[i] = Cf[3 * i] * FCC_S[a][0] + Cf[3 * i + 1] * FCC_S[a][1] + Cf[3 * i + 2] * FCC_S[a][2];
-      w[i] = e.Minv[i] * FCC_M[a][0] + e.Minv[3 + i] * FCC_M[a][1] + e.Minv[6 + i] * FCC_M[a][2];
+      bool fu = true, fw = true;
+      u[i] = w[i] = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        u[i] = cacc(u[i], fu, fcc_s(a, k), Cf[3 * i + k]);
+        w[i] = cacc(w[i], fw, fcc_m(a, k), e.Minv[3 * k + i]);
+      }
     }
     const double f = -gp * INV_SQRT6;
     double T[6] = {f * u[0] * w[0], f * u[1] * w[1], f * u[2] * w[2], 0.5 * f * (u[1] * w[2] + u[2] * w[1]),
                    0.5 * f * (u[0] * w[2] + u[2] * w[0]), 0.5 * f * (u[0] * w[1] + u[1] * w[0])};
     double cv[6];
     cubic(c, T, cv);
-    double wt[6];
-    tau_grad(a, wt);
+    // J -= cv (x) d tau^a / dS, skipping the zero coefficients
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
-      for (int j = 0; j < 6; ++j) J[6 * i + j] = fma(-cv[i], wt[j], J[6 * i + j]);
+      for (int j = 0; j < 6; ++j)
+        if (tau_coef(a, j) != 0) J[6 * i + j] = fma(-cv[i], (double)tau_coef(a, j) * INV_SQRT6, J[6 * i + j]);
   }
 }
 

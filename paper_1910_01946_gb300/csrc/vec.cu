@@ -431,11 +431,7 @@ __global__ void __launch_bounds__(128) k_commit(size_t nvox, const int32_t* __re
 #pragma unroll
   for (int a = 0; a < 12; ++a) {
     const double d = dgam[a * nvox + v];
-    const double gs = d * 0.40824829046386301637;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) M[3 * i + j] = fma(gs, (double)(FCC_S[a][i] * FCC_M[a][j]), M[3 * i + j]);
+    add_schmid(M, a, d);
     const double ad = fabs(d);
     const double r0 = rho[a * nvox + v];
     rho[a * nvox + v] = (r0 + ad / (b * ell[a * nvox + v])) / (1.0 + 2.0 * yc * ad / b);
