@@ -148,10 +148,15 @@ __device__ void evaluate(const Consts& c, const double* S, const double* A, cons
   e.rn = (fin && isfinite(rn)) ? rn : INFINITY;
 }
 
-// J = I - sum_a c^a (x) w^a with c^a = -dgp^a C : sym(Ce S0^a Minv)
+// J = I - sum_a c^a (x) w^a with c^a = -dgp^a C : sym(Ce S0^a Minv) and w^a =
+// d tau^a / dS.  C is linear, so the sum is accumulated before it:
+// J = I - C : N, N = sum_a T^a (x) w^a, T^a = -dgp^a sym(Ce S0^a Minv), and
+// the cubic stiffness is applied to the six columns of N once instead of to
+// each system's T^a.
 __device__ void jacobian(const Consts& c, const Eval& e, const double* tinv, double dt, double* J, double* dgp) {
+  double N[36];
 #pragma unroll
-  for (int i = 0; i < 36; ++i) J[i] = (i % 7 == 0) ? 1.0 : 0.0;
+  for (int i = 0; i < 36; ++i) N[i] = 0.0;
   double Cf[9];
   sym_full(e.Ce, Cf);
 #pragma unroll
@@ -173,16 +178,23 @@ __device__ void jacobian(const Consts& c, const Eval& e, const double* tinv, dou
       }
     }
     const double f = -gp * INV_SQRT6;
-    double T[6] = {f * u[0] * w[0], f * u[1] * w[1], f * u[2] * w[2], 0.5 * f * (u[1] * w[2] + u[2] * w[1]),
-                   0.5 * f * (u[0] * w[2] + u[2] * w[0]), 0.5 * f * (u[0] * w[1] + u[1] * w[0])};
-    double cv[6];
-    cubic(c, T, cv);
-    // J -= cv (x) d tau^a / dS, skipping the zero coefficients
+    const double T[6] = {f * u[0] * w[0], f * u[1] * w[1], f * u[2] * w[2], 0.5 * f * (u[1] * w[2] + u[2] * w[1]),
+                         0.5 * f * (u[0] * w[2] + u[2] * w[0]), 0.5 * f * (u[0] * w[1] + u[1] * w[0])};
+    // N += T (x) d tau^a / dS, skipping the zero coefficients
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
       for (int j = 0; j < 6; ++j)
-        if (tau_coef(a, j) != 0) J[6 * i + j] = fma(-cv[i], (double)tau_coef(a, j) * INV_SQRT6, J[6 * i + j]);
+        if (tau_coef(a, j) != 0) N[6 * i + j] = fma(T[i], (double)tau_coef(a, j) * INV_SQRT6, N[6 * i + j]);
+  }
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    double col[6], cc[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) col[i] = N[6 * i + j];
+    cubic(c, col, cc);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) J[6 * i + j] = (i == j) ? 1.0 - cc[i] : -cc[i];
   }
 }
 
@@ -474,11 +486,25 @@ __global__ void __launch_bounds__(128) k_local(
 
 // The consistent tangent at the converged S: the same work for every voxel
 // (no data-dependent iterations), so whole warps stay converged.
-__global__ void __launch_bounds__(128) k_tangent(
+//
+// For a direction dF~ = a b^T of the crystal-frame deformation gradient,
+// dE = sym(u w^T) with u = Fe^T a, w = Fp^-T b, and
+//   dP~ = F~ dQ + a (Q b)^T,  dQ = Fp^-1 dS Fp^-T - (dFpi W + (dFpi W)^T),
+// where dS = J^-1 C : dE, dM = sum_a dgp^a tau^a(dS) s^a (x) m^a,
+// dFpi = Fp^-1 dM M^-1, W = S Fp^-T and Q = Fp^-1 S Fp^-T.  Everything but
+// a (Q b)^T is linear in the six components of dE, so F~ dQ is formed once
+// for each unit dE (the columns of H, 9 x 6, in shared memory) and each of
+// the nine directions costs H dE plus the rank-one term and the rotation:
+// six solves through the chain instead of nine.
+constexpr int TAN_THREADS = 64;
+
+__global__ void __launch_bounds__(TAN_THREADS) k_tangent(
     size_t nvox, const int32_t* __restrict__ grain, const double* __restrict__ grainR,
     const double* __restrict__ Fin, const double* __restrict__ xdir, double lambda,
     const double* __restrict__ Fp0inv, const double* __restrict__ tauc_g, const double* __restrict__ Sin,
     double* __restrict__ Kout, double dt, Consts c, int k32) {
+  __shared__ double Hs[54 * TAN_THREADS];     // H[9 m + ij] of this thread at Hs[(9 m + ij) T + tid]
+  double* H = Hs + threadIdx.x;
   const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v < nvox) {
     VoxelIn in;
@@ -502,28 +528,20 @@ __global__ void __launch_bounds__(128) k_tangent(
     sym_full(S, Sf);
     mat3_mult(Sf, Fpinv, W);             // W = S Fpinv^T
     mat3_mul(Fpinv, W, Q);               // Q = Fpinv S Fpinv^T
+    // H: F~ dQ for the six unit strain increments (tensor components
+    // E11, E22, E33, E23, E13, E12, as `cubic` takes them)
 #pragma unroll 1
-    for (int kl = 0; kl < 9; ++kl) {
-      const int kk = kl / 3, ll = kl % 3;
-      double a3[3], b3[3];
+    for (int m = 0; m < 6; ++m) {
+      double dE[6];
 #pragma unroll
-      for (int p = 0; p < 3; ++p) { a3[p] = R[3 * kk + p]; b3[p] = R[3 * ll + p]; }
-      // dF~ = a b^T; dEe = sym(Fe^T a (Fpinv^T b)^T)
-      double u[3], w[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        u[i] = Fe[i] * a3[0] + Fe[3 + i] * a3[1] + Fe[6 + i] * a3[2];
-        w[i] = Fpinv[i] * b3[0] + Fpinv[3 + i] * b3[1] + Fpinv[6 + i] * b3[2];
-      }
-      double dE[6] = {u[0] * w[0], u[1] * w[1], u[2] * w[2], 0.5 * (u[1] * w[2] + u[2] * w[1]),
-                      0.5 * (u[0] * w[2] + u[2] * w[0]), 0.5 * (u[0] * w[1] + u[1] * w[0])};
+      for (int k = 0; k < 6; ++k) dE[k] = k == m ? 1.0 : 0.0;
       double dS[6];
       cubic(c, dE, dS);
       lu6_solve(J, piv, dS);
       double dM[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
       for (int a = 0; a < 12; ++a) add_schmid(dM, a, dgp[a] * resolved(dS, a));
-      double t1[9], dFpi[9], dQ[9], dSf[9], t2[9];
+      double t1[9], dFpi[9], dQ[9], dSf[9], t2[9], dPt[9];
       mat3_mul(dM, e.Minv, t1);
       mat3_mul(Fpinv, t1, dFpi);        // (negated below)
       mat3_mul(dFpi, W, t1);            // dFpinv W with dFpinv = -dFpi
@@ -534,15 +552,36 @@ __global__ void __launch_bounds__(128) k_tangent(
       for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) dQ[3 * i + j] -= t1[3 * i + j] + t1[3 * j + i];
+      mat3_mul(Ft, dQ, dPt);
+#pragma unroll
+      for (int ij = 0; ij < 9; ++ij) H[(9 * m + ij) * TAN_THREADS] = dPt[ij];
+    }
+#pragma unroll 1
+    for (int kl = 0; kl < 9; ++kl) {
+      const int kk = kl / 3, ll = kl % 3;
+      double a3[3], b3[3];
+#pragma unroll
+      for (int p = 0; p < 3; ++p) { a3[p] = R[3 * kk + p]; b3[p] = R[3 * ll + p]; }
+      // dF~ = a b^T; dE = sym(Fe^T a (Fpinv^T b)^T)
+      double u[3], w[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        u[i] = Fe[i] * a3[0] + Fe[3 + i] * a3[1] + Fe[6 + i] * a3[2];
+        w[i] = Fpinv[i] * b3[0] + Fpinv[3 + i] * b3[1] + Fpinv[6 + i] * b3[2];
+      }
+      const double dE[6] = {u[0] * w[0], u[1] * w[1], u[2] * w[2], 0.5 * (u[1] * w[2] + u[2] * w[1]),
+                            0.5 * (u[0] * w[2] + u[2] * w[0]), 0.5 * (u[0] * w[1] + u[1] * w[0])};
       double qb[3];
 #pragma unroll
       for (int j = 0; j < 3; ++j) qb[j] = Q[3 * j] * b3[0] + Q[3 * j + 1] * b3[1] + Q[3 * j + 2] * b3[2];
       double dPt[9];
-      mat3_mul(Ft, dQ, dPt);
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
+      for (int ij = 0; ij < 9; ++ij) {
+        double t = a3[ij / 3] * qb[ij % 3];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) dPt[3 * i + j] = fma(a3[i], qb[j], dPt[3 * i + j]);
+        for (int m = 0; m < 6; ++m) t = fma(H[(9 * m + ij) * TAN_THREADS], dE[m], t);
+        dPt[ij] = t;
+      }
       double U[9], dP[9];
       mat3_mult(dPt, R, U);
       mat3_mul(R, U, dP);
@@ -825,11 +864,11 @@ cudaError_t launch_local(const rve_s* h, double dt, double lambda, int out_buf, 
 }
 
 cudaError_t launch_tangent(const rve_s* h, double dt, double lambda, int buf, cudaStream_t s) {
-  const unsigned blocks = (unsigned)((h->nvox + 127) / 128);
+  const unsigned blocks = (unsigned)((h->nvox + TAN_THREADS - 1) / TAN_THREADS);
   {
     ProfScope ps_(h, RVE_K_TANGENT_BUILD, s);
-    k_tangent<<<blocks, 128, 0, s>>>(h->nvox, h->grain, h->grainR, h->F, h->x, lambda, h->Fp0inv, h->tauc,
-                                     h->S[buf], h->K[buf], dt, h->cst, h->opt.precision == 1);
+    k_tangent<<<blocks, TAN_THREADS, 0, s>>>(h->nvox, h->grain, h->grainR, h->F, h->x, lambda, h->Fp0inv,
+                                             h->tauc, h->S[buf], h->K[buf], dt, h->cst, h->opt.precision == 1);
   }
   return cudaGetLastError();
 }
