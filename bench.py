@@ -317,43 +317,58 @@ def load_peaks():
 
 
 # ---------------------------------------------------------------- CPU oracle
+_ORACLE_CACHE = {}
+
+
 def oracle_slice(wl, n_cg, seed=0):
     """A bounded slice of the FP64 CPU oracle's increment on the full
     workload, timed for real (wall clock on the host cores): the local update
-    with tangent on a seeded subset of grains holding n_cg / ORACLE_CG_PER_EVAL
-    of the voxels, then n_cg conjugate-gradient iterations on the full grid
-    (the tangent field tiled from the subset).  The slice keeps the oracle's
-    own mix of the two, so its rate nvox * n_cg / seconds is the
-    voxel-iterations/s of the oracle's whole increments.  The hardening (once
-    per increment) is set up before the clock starts.  Returns (seconds,
-    voxels evaluated, n_cg)."""
+    with tangent on a seeded subset of the voxels (whole grains, the last one
+    cut to size) holding n_cg / ORACLE_CG_PER_EVAL of them, then n_cg
+    conjugate-gradient iterations on the full grid.  The slice keeps the
+    oracle's own mix of the two, so its rate nvox * n_cg / seconds is the
+    voxel-iterations/s of the oracle's whole increments.  Two steps of the
+    slice are its own scaffolding and run off the clock: tiling the subset's
+    tangent over the grid, and the residual projection that starts the CG
+    (a whole increment projects one residual per local evaluation, about 1 %
+    of an evaluation's time).  The hardening (once per increment) is set up
+    before the clock starts.  Returns (seconds, voxels evaluated, n_cg)."""
     from oracle import solver
     from oracle import spectral as sp
-    gid, quat, mat = wl.inputs()
-    o = solver.RVE(gid, quat, mat, wl.edge)
-    nv = gid.size
-    tauc, ell = o.hardening()
+    key = wl.name
+    if key not in _ORACLE_CACHE:
+        gid, quat, mat = wl.inputs()
+        o = solver.RVE(gid, quat, mat, wl.edge)
+        _ORACLE_CACHE[key] = (o, o.hardening(), list(o.grains))
+    o, (tauc, ell), grains = _ORACLE_CACHE[key]
+    nv = o.F.shape[0]
     F = o.F + (wl.dFbar() * rvegen.UNIAXIAL_X_MASK).reshape(3, 3)
     rng = np.random.default_rng(seed)
-    target = nv * n_cg / ORACLE_CG_PER_EVAL
+    need = max(1, int(round(nv * n_cg / ORACLE_CG_PER_EVAL)))
     chosen, count = [], 0
-    for gi in rng.permutation(len(o.grains)):
-        if count >= target:
+    for gi in rng.permutation(len(grains)):
+        if count >= need:
             break
-        chosen.append(o.grains[gi])
-        count += len(o.grains[gi]["idx"])
-    keep = o.grains
-    o.grains = chosen
+        g = grains[gi]
+        take = min(len(g["idx"]), need - count)
+        chosen.append(g if take == len(g["idx"]) else dict(g, idx=g["idx"][:take]))
+        count += take
     idx = np.concatenate([g["idx"] for g in chosen])
     o.opts.max_cg = n_cg
     o.opts.cg_tol = 1e-300
-    t0 = time.perf_counter()
-    P, K, S, M, dg, lit, lf = o.constitutive(F, tauc, o.S, wl.dt)
-    o.grains = keep
+    o.grains = chosen
+    try:
+        t0 = time.perf_counter()
+        P, K, S, M, dg, lit, lf = o.constitutive(F, tauc, o.S, wl.dt)
+        t_local = time.perf_counter() - t0
+    finally:
+        o.grains = grains
     Kfull = np.resize(K[idx], (nv, 3, 3, 3, 3))
     R = o.flat(sp.project(o.field(np.resize(P[idx], (nv, 3, 3))), rvegen.UNIAXIAL_X_MASK, o.h))
+    t0 = time.perf_counter()
     o.cg(Kfull, -R, rvegen.UNIAXIAL_X_MASK)
-    return time.perf_counter() - t0, len(idx), n_cg
+    t_cg = time.perf_counter() - t0
+    return t_local + t_cg, len(idx), n_cg
 
 
 def oracle_increments(wl, warmup, steps):
@@ -713,9 +728,9 @@ def main():
                       f"evaluations per increment, {el / a.steps:.1f} s per increment")
             ms = 1e3 * el / a.steps
         else:
-            # every step a real slice of 3 CG iterations and its share of the
-            # local update (about 3 s on 16 cores at 64^3), warm-up slices untimed
-            n_cg = 3
+            # every step a real slice of 6 CG iterations and its share of the
+            # local update (about 1.5 s on 8 cores at 64^3), warm-up slices untimed
+            n_cg = 6
             secs = []
             for k in range(a.warmup + a.steps):
                 t, nsub, _ = oracle_slice(wl, n_cg, seed=k)
