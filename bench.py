@@ -298,13 +298,15 @@ def mixed_accuracy(pkg, rve, wl, gid, quat, mat, dev, a, P_hist):
 # capture have no entry (reported as null), as do other grid sizes.
 TRAFFIC_SOURCE = "profiles/kernels_cu64.md"
 TRAFFIC_64 = {
-    ("tangent_apply", 0): 207.66e6 + 5.10e6,   # K : p reads its algorithmic 207.6 MB
-    ("tangent_apply", 1): 103.84e6 + 3.53e6,   # TMA-staged FP32 apply (float K, r, p)
-    ("constitutive", 0): 98.92e6 + 50.16e6,    # k_local (the same kernel in both precisions)
-    ("constitutive", 1): 98.92e6 + 50.16e6,
-    ("tangent_build", 0): 78.10e6 + 211.22e6,  # k_tangent, K written in FP64
-    ("stencil", 0): 18.94e6,                   # k_div (its writes stay in L2)
-    ("cg_update", 0): 62.95e6 + 0.11e6,        # k_grad_t<true>
+    ("tangent_apply", 0): 207.66e6 + 5.11e6,   # K : p reads its algorithmic 207.6 MB
+    ("tangent_apply", 1): 103.84e6 + 3.36e6,   # TMA-staged FP32 apply (float K, r, p)
+    ("constitutive", 0): 97.20e6 + 30.14e6,    # k_local (the same kernel in both precisions)
+    ("constitutive", 1): 97.20e6 + 30.14e6,
+    ("tangent_build", 0): 77.53e6 + 149.33e6,  # k_tangent, K written in FP64
+    ("stencil", 0): 18.94e6,                   # k_div_rows (its writes stay in L2)
+    ("stencil", 1): 9.49e6,                    # k_div_rows<float>
+    ("cg_update", 0): 62.96e6 + 0.16e6,        # k_grad_rows<true>
+    ("cg_update", 1): 31.49e6,                 # k_grad_rows<true, float>
 }
 
 
