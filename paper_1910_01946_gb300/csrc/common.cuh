@@ -236,10 +236,28 @@ __device__ __forceinline__ bool last_block_sums(const double* partial, int nval,
   double acc[9];
 #pragma unroll
   for (int c = 0; c < 9; ++c) acc[c] = 0.0;
-  for (int i = t; i < (int)gridDim.x; i += lin_nthreads()) {
+  // four partials per value in flight at a time (the loads of one group are
+  // issued before its additions, which keep the order of i: the sums are
+  // those of the plain loop, bit for bit)
+  const int n = (int)gridDim.x, nt = lin_nthreads();
+  int i = t;
+  for (; i + 3 * nt < n; i += 4 * nt) {
+    double v[4][9];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < 9; ++c)
+        v[q][c] = (c < nval && ((which >> c) & 1u)) ? __ldcg(partial + (size_t)c * n + i + q * nt) : 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < 9; ++c)
+        if (c < nval && ((which >> c) & 1u)) acc[c] += v[q][c];
+  }
+  for (; i < n; i += nt) {
 #pragma unroll
     for (int c = 0; c < 9; ++c)
-      if (c < nval && ((which >> c) & 1u)) acc[c] += __ldcg(partial + (size_t)c * gridDim.x + i);
+      if (c < nval && ((which >> c) & 1u)) acc[c] += __ldcg(partial + (size_t)c * n + i);
   }
   double res[9];
   blk_sums9<double>(acc, which & ((1u << nval) - 1u), sh, res);

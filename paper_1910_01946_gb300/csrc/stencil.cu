@@ -466,7 +466,8 @@ __global__ void __launch_bounds__(32 * RW, NPL <= 2 ? 4 : 1) k_grad_rows(Grid3 g
   const V alpha = CG ? (V)ds[DS_ALPHA] : (V)0;
   V off[9];
 #pragma unroll
-  for (int c = 0; c < 9; ++c) off[c] = zm.keep[c] ? (V)(ds[DS_XMEAN + c] + zm.add[c]) : (V)0;
+  for (int c = 0; c < 9; ++c)          // (in the CG update the zero mode carries no shift)
+    off[c] = zm.keep[c] ? (CG ? (V)ds[DS_XMEAN + c] : (V)(ds[DS_XMEAN + c] + zm.add[c])) : (V)0;
   const int lane = threadIdx.x & 31;
   const int right = (lane + 1) & 31;
   V acc = (V)0;
