@@ -809,7 +809,7 @@ rve_status rve_create(const int32_t* grain_id, int n0, int n1, int n2, const dou
   if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || h->num_sms < 1)
     h->num_sms = 152;
   h->div_blocks = 4 * h->num_sms;
-  h->fft_fill = 4 * h->num_sms;
+  h->fft_fill = 8 * h->num_sms;     // x passes: radix-8 rows leave 8 threads per row, so more, smaller tiles
   h->fft_fill_y = 8 * h->num_sms;   // the y passes run faster with smaller tiles (measured at 64^3)
   h->fft_fill_z = 4 * h->num_sms;
   h->tma_apply = opt->tma != 0 && opt->precision == 1 && vec_init() == cudaSuccess;
