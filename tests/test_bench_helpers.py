@@ -54,3 +54,31 @@ def test_hall_petch_fit_recovers_known_law():
     assert abs(Cf / C - 1) < 1e-12 and abs(xf - x) < 1e-12
     # no strengthening at some size: nothing to fit
     assert b.hall_petch_fit(d, s_inf, s_inf, rho) is None
+
+
+def test_oracle_slice_takes_the_oracle_mix_exactly():
+    # the slice evaluates n_cg / ORACLE_CG_PER_EVAL of the voxels (the last
+    # grain cut to size) and times real oracle work
+    import rvegen
+    m = bench()
+    wl = rvegen.WORKLOADS["cu16"]
+    n_cg = 6
+    secs, nsub, n = m.oracle_slice(wl, n_cg, seed=3)
+    assert n == n_cg and secs > 0.0
+    assert nsub == round(wl.n ** 3 * n_cg / m.ORACLE_CG_PER_EVAL)
+    # a second slice reuses the set-up oracle and picks another subset size-for-size
+    secs2, nsub2, _ = m.oracle_slice(wl, n_cg, seed=4)
+    assert nsub2 == nsub and secs2 > 0.0
+
+
+def test_reference_arm_prints_one_line():
+    import json
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "cu16", "--steps", "2", "--warmup", "1"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 2
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
