@@ -128,11 +128,15 @@ class ClockSampler:
 # (an FMA counts 2; constant Schmid-tensor entries 0 and +-1 folded).  k_local:
 # per voxel set-up (frame rotation, trial elastic state) and P at the
 # converged S (six 3x3 products), per residual evaluation, per Newton
-# iteration (Jacobian, LU, solve).  k_tangent: per voxel set-up, one
-# evaluation, Jacobian and LU, the intermediate products, and the nine
-# directions of dP/dF.
-CONST_SETUP, CONST_EVAL, CONST_ITER = 180.0 + 270.0, 500.0, 1532.0
-TANGENT_FLOPS = 180.0 + 500.0 + 1320.0 + 146.0 + 180.0 + 9 * 780.0
+# iteration (Jacobian with the stiffness applied once per column of the
+# accumulated sum, LU, solve).  k_tangent: per voxel set-up, one evaluation,
+# Jacobian and LU, the intermediate products, the strain-linear response to
+# each of the six unit strains (solve, Schmid sum, five 3x3 products, F~ dQ)
+# and the nine directions of dP/dF (Fe^T a and Fp^-T b, dE, H dE, the
+# rank-one term and the rotation).  The k_tangent total, 7744, agrees with
+# the FP64 operations ncu counts for the kernel (7771 per voxel).
+CONST_SETUP, CONST_EVAL, CONST_ITER = 180.0 + 270.0, 500.0, 1442.0
+TANGENT_FLOPS = 180.0 + 500.0 + 1230.0 + 146.0 + 180.0 + 6 * 522.0 + 9 * 264.0
 CONST_BYTES = 364 + 216        # reads F, dF, Fp^-1, tauc, S, grain; writes S, dgam, P
 TANGENT_BYTES = 364 + 648      # reads F, dF, Fp^-1, tauc, S, grain; writes K
 
